@@ -1,0 +1,246 @@
+/*
+ * ising.h -- C ABI of the GB300 checkerboard Metropolis library (libising_gb300.so).
+ *
+ * The library simulates the 2D nearest-neighbour Ising model
+ *     H(sigma) = -J sum_<ij> sigma_i sigma_j - mu sum_i sigma_i,  mu = 0, J = 1,
+ * on an L x L torus (paper Sec. 3) with the checkerboard Metropolis-within-Gibbs
+ * sweep of Sec. 3.1: every black site (i+j even) is updated with the white sites
+ * fixed, then every white site with the black sites fixed; a site with
+ * h = sigma_i * nn(i) flips with probability min{1, exp(-2 beta h)}.
+ * One "sweep" is one black plus one white half-sweep (the unit of the paper's
+ * flips/ns, Sec. 4.2).
+ *
+ * Determinism.  The chain is a pure function of (L, beta, seed, start state,
+ * sweep count):
+ *   - uniform draw of site (i,j) of colour c in sweep s: output word (p & 3) of
+ *     Philox4x32-10 (Salmon et al., SC'11) with key (seed lo32, seed hi32) and
+ *     counter (q lo32, q hi32, s, c), where p = i*(L/2) + (j>>1), q = p >> 2;
+ *   - flip iff h <= 0, or word < T_h with T_h = min(2^32, ceil(exp(-2 beta h) 2^32))
+ *     computed on the host in FP64 (see ising_thresholds);
+ *   - hot start: sigma = +1 iff the word drawn with s = 0xFFFFFFFF is < 2^31;
+ *     cold start: all +1.
+ *   Both kernels (bit-packed and int8) produce the same lattice bit for bit.
+ *
+ * Observables after each sweep: M = sum_i sigma_i and E = H(sigma) as exact
+ * 64-bit integers (Sec. 4.1 magnetisation; E from the Sec. 3 Hamiltonian).
+ *
+ * Conventions for every function:
+ *   - returns ISING_OK (0) or a negative ISING_E* code; outputs are written only
+ *     on ISING_OK; ising_last_error() returns a thread-local message for the
+ *     last failure on the calling thread;
+ *   - host pointers are caller-owned and only read/written during the call;
+ *   - handles own all device memory they allocate (cudaMalloc) and release it in
+ *     the matching *_free; a handle must not be used from two threads at once,
+ *     distinct handles may;
+ *   - work is enqueued on the handle's CUDA stream; functions that return data
+ *     to the host synchronise that stream.
+ */
+#ifndef ISING_GB300_H
+#define ISING_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ISING_OK 0
+#define ISING_EINVAL (-1)   /* bad argument (size, beta, index, null pointer) */
+#define ISING_ENOMEM (-2)   /* device allocation or HBM budget exhausted */
+#define ISING_ECUDA (-3)    /* CUDA runtime error (message in ising_last_error) */
+#define ISING_ETIMEOUT (-4) /* a kernel's bounded wait expired; results invalid */
+#define ISING_EBUSY (-5)    /* slot table full */
+
+#define ISING_HOT 0
+#define ISING_COLD 1
+
+#define ISING_PACKED 0 /* multi-spin-coded black/white bit planes; L % 64 == 0 */
+#define ISING_INT8 1   /* row-major int8 +1/-1 lattice; L % 8 == 0 */
+
+typedef struct ising_s *ising_t;
+typedef struct ising_batch_s *ising_batch_t;
+
+/* Thread-local description of the last error on this thread ("" if none). */
+const char *ising_last_error(void);
+
+/* Library version string. */
+const char *ising_version(void);
+
+/*
+ * Acceptance thresholds (Sec. 3.1 acceptance rule, Algorithm 1-2's
+ * exp(-2 nn sigma) with beta restored): T[0] for h = 2, T[1] for h = 4,
+ * T_h = min(2^32, ceil(exp(-2 beta h) * 2^32)) in FP64 with the host libm exp.
+ * A uniform 32-bit word x accepts iff x < T_h.  beta must be finite and >= 0.
+ * Host-only; needs no GPU.  Errors: EINVAL.
+ */
+int ising_thresholds(double beta, uint64_t T[2]);
+
+/* ------------------------------------------------------------------------
+ * Single lattice
+ * ---------------------------------------------------------------------- */
+
+/*
+ * Creates a lattice of side L at inverse temperature beta with Philox seed
+ * `seed`: hot start, bit-packed kernel, default stream.  Equivalent to
+ * ising_init_ex(out, L, beta, seed, ISING_HOT, ISING_PACKED, NULL).
+ */
+int ising_init(ising_t *out, int64_t L, double beta, uint64_t seed);
+
+/*
+ * start: ISING_HOT or ISING_COLD.  kernel: ISING_PACKED (L % 64 == 0, 64 <= L <=
+ * 1048576) or ISING_INT8 (L % 8 == 0, 8 <= L <= 131072).  stream: a cudaStream_t
+ * on which all of this handle's work is enqueued (the caller keeps it alive
+ * until ising_free); NULL makes the handle create and own a non-blocking stream.  Device memory: packed L*L/8
+ * bytes, int8 L*L bytes, plus 16 bytes of history per sweep (grown on demand).
+ * Errors: EINVAL (L, beta, start, kernel), ENOMEM, ECUDA.
+ */
+int ising_init_ex(ising_t *out, int64_t L, double beta, uint64_t seed, int start, int kernel, void *stream);
+
+/*
+ * Enqueues n sweeps (n >= 0) on the handle's stream; returns without waiting.
+ * The sweep counter advances by n (total must stay below 2^32 - 1) and the
+ * per-sweep (M, E) history grows by n entries.  Errors: EINVAL, ENOMEM, ECUDA.
+ */
+int ising_sweep(ising_t h, int64_t n);
+
+/*
+ * Current M and E (after the last sweep; the start state if none) and the
+ * number of sweeps done.  Synchronises.  Any output pointer may be NULL.
+ * Errors: EINVAL, ECUDA, ETIMEOUT.
+ */
+int ising_observables(ising_t h, int64_t *M, int64_t *E, int64_t *sweeps_done);
+
+/*
+ * Copies history entries first .. first+count-1 (sweep indices, 0-based) into
+ * the caller's arrays M[count] and E[count] (either may be NULL).  Synchronises.
+ * Errors: EINVAL (range beyond sweeps done), ECUDA, ETIMEOUT.
+ */
+int ising_history(ising_t h, int64_t first, int64_t count, int64_t *M, int64_t *E);
+
+/*
+ * Sec. 4.1 observables over samples s = burn_in .. sweeps_done-1, from exact
+ * integer sums on the device: out[0] = <|m|>, out[1] = <m^2>, out[2] = <m^4>,
+ * out[3] = <e> (E/N), out[4] = <e^2>, out[5] = U4 = 1 - <m^4>/(3 <m^2>^2).
+ * sums (may be NULL) receives the 11 exact 64-bit limbs: sum|M|, sum M^2 (2
+ * limbs, little-endian), sum M^4 (4), sum E (2, two's complement), sum E^2 (2).
+ * Synchronises.  Errors: EINVAL (no samples), ECUDA.
+ */
+int ising_moments(ising_t h, int64_t burn_in, double out[6], uint64_t sums[11]);
+
+/* Copies the lattice into out[L*L] (row-major, +1 / -1).  Synchronises. */
+int ising_get_lattice(ising_t h, int8_t *out);
+
+/*
+ * Replaces the lattice by in[L*L] (row-major, each entry +1 or -1; other values
+ * are EINVAL).  Does not change the sweep counter.  Synchronises.
+ */
+int ising_set_lattice(ising_t h, const int8_t *in);
+
+/*
+ * Packed handles only: copy the bit planes to / from host arrays of L*L/64
+ * uint32 words each (row i, word w at index i*(L/64) + w; bit b is site
+ * (i, 2(32w+b) + ((i+c)&1)) of colour c; 1 = +1).  Synchronises.
+ */
+int ising_get_planes(ising_t h, uint32_t *black, uint32_t *white);
+int ising_set_planes(ising_t h, const uint32_t *black, const uint32_t *white);
+
+/*
+ * Checkpoint: ising_state_bytes gives the size of the blob; ising_save writes
+ * (L, beta, seed, kernel, sweeps done, lattice, history) into buf; ising_load
+ * creates a new handle that continues the same chain bit for bit.
+ */
+int ising_state_bytes(ising_t h, int64_t *bytes);
+int ising_save(ising_t h, void *buf, int64_t bytes);
+int ising_load(ising_t *out, const void *buf, int64_t bytes, void *stream);
+
+/* Waits for the handle's work; reports ETIMEOUT if a kernel gave up. */
+int ising_synchronize(ising_t h);
+
+/* Releases the handle and its device memory (NULL is a no-op). */
+int ising_free(ising_t h);
+
+/* ------------------------------------------------------------------------
+ * Batch: many packed lattices of uneven L and beta swept by one persistent
+ * launch per half-sweep (the single-device analogue of the paper's replicated
+ * program, Sec. 5), optionally replayed from a captured CUDA graph.
+ * ---------------------------------------------------------------------- */
+
+/*
+ * Creates an empty batch that can hold up to `capacity` lattices of side <=
+ * max_L with `arena_bytes` of device memory for planes and histories (the HBM
+ * budget; allocation beyond it is ENOMEM).  threads: CTA size of the sweep
+ * kernel (128, 256 or 512; 0 = 256).  stream as in ising_init_ex.
+ */
+int ising_batch_create(ising_batch_t *out, int32_t capacity, int64_t max_L, int64_t arena_bytes, int32_t threads,
+                       void *stream);
+
+/*
+ * Adds a packed lattice (L % 64 == 0, L <= max_L) that will run `sweeps`
+ * sweeps at most (its history capacity).  tile_rows: rows per tile (4, 8, 16,
+ * 32 or 64 dividing L; 0 = built-in choice).  Writes the slot index to *idx.
+ * Enqueues the start state.  Errors: EINVAL, ENOMEM (arena), EBUSY (slots).
+ */
+int ising_batch_add(ising_batch_t b, int64_t L, double beta, uint64_t seed, int32_t start, int64_t sweeps,
+                    int32_t tile_rows, int32_t *idx);
+
+/* Frees a slot and its arena memory (after the stream's pending work). */
+int ising_batch_remove(ising_batch_t b, int32_t idx);
+
+/*
+ * Enqueues `sweeps` sweeps of every lattice in the batch; a lattice stops at
+ * its own sweep limit.  graph_sweeps > 0: capture graph_sweeps sweeps into a
+ * CUDA graph once (re-captured if graph_sweeps changes) and replay it
+ * sweeps / graph_sweeps times (sweeps must be a multiple); 0: plain launches.
+ */
+int ising_batch_run(ising_batch_t b, int64_t sweeps, int32_t graph_sweeps);
+
+/* Per-lattice sweeps done (synchronises). */
+int ising_batch_sweeps_done(ising_batch_t b, int32_t idx, int64_t *sweeps_done);
+
+int ising_batch_observables(ising_batch_t b, int32_t idx, int64_t *M, int64_t *E, int64_t *sweeps_done);
+int ising_batch_history(ising_batch_t b, int32_t idx, int64_t first, int64_t count, int64_t *M, int64_t *E);
+int ising_batch_moments(ising_batch_t b, int32_t idx, int64_t burn_in, double out[6], uint64_t sums[11]);
+int ising_batch_get_lattice(ising_batch_t b, int32_t idx, int8_t *out);
+
+/* Arena bytes in use and slots in use. */
+int ising_batch_usage(ising_batch_t b, int64_t *arena_used, int32_t *slots_used);
+
+/* Waits for the batch's work; ETIMEOUT if a kernel gave up. */
+int ising_batch_synchronize(ising_batch_t b);
+
+int ising_batch_free(ising_batch_t b);
+
+/*
+ * Times one half-sweep of a packed lattice of side L for each candidate
+ * (tile_rows in {4,8,16,32,64} dividing L, threads in {256, 512}) and returns
+ * the fastest in *tile_rows, *threads and its time in *ms.  Uses its own
+ * scratch lattice.  Errors: EINVAL, ENOMEM, ECUDA.
+ */
+int ising_autotune(int64_t L, int32_t *tile_rows, int32_t *threads, double *ms);
+
+/* ------------------------------------------------------------------------
+ * Device-side building blocks on caller-owned device memory (for tests and
+ * for callers that manage memory themselves).  All pointers are device
+ * pointers; work is enqueued on `stream` and not waited for.
+ * ---------------------------------------------------------------------- */
+
+/*
+ * Philox4x32-10 of counters (ctr0 + k as a 64-bit value in words 0-1, ctr[2],
+ * ctr[3]) for k = 0 .. nblocks-1 under key `key`; out[4*nblocks] (device).
+ */
+int ising_dev_philox(uint64_t key, const uint32_t ctr[4], int64_t nblocks, uint32_t *out, void *stream);
+
+/*
+ * Integer-pipe throughput of this GPU, the denominator of the sweep's ALU
+ * roofline: out[0] = 32x32->64 multiplies (both halves used, as in a Philox
+ * round) per SM per clock; out[1] = ALU ops (3-input XOR, funnel shift) per SM
+ * per clock.  Runs two short compute-only kernels and synchronises the device.
+ * Not part of the paper: measurement support.  Errors: ENOMEM, ECUDA.
+ */
+int ising_probe_int_rates(double out[2]);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ISING_GB300_H */

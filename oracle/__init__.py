@@ -25,6 +25,11 @@ from fractions import Fraction
 
 import numpy as np
 
+# libgomp reads this when the library loads: threads that wait at the end of a
+# parallel region sleep instead of spinning, so a busy host does not stall the
+# short per-half-sweep regions of small lattices.
+os.environ.setdefault("OMP_WAIT_POLICY", "PASSIVE")
+
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "ising_oracle.c")
 _LIB_PATH = os.path.join(_HERE, "_ising_oracle.so")
@@ -79,6 +84,12 @@ def lib():
                                         ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
                                         ctypes.c_int64, ctypes.c_int64, i8p]
             L.oracle_window.restype = ctypes.c_int
+            L.oracle_init_rows.argtypes = [i8p, ctypes.c_int64, ctypes.c_uint64, ctypes.c_int, ctypes.c_int64,
+                                           ctypes.c_int64]
+            L.oracle_init_rows.restype = None
+            L.oracle_half_sweep_rows.argtypes = [i8p, ctypes.c_int64, ctypes.c_int, ctypes.c_double,
+                                                 ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int64, ctypes.c_int64]
+            L.oracle_half_sweep_rows.restype = ctypes.c_int64
             _lib = L
     return _lib
 
@@ -162,6 +173,19 @@ def window(L: int, beta: float, seed: int, start: int, sweeps: int, i0: int, j0:
     if rc != 0:
         raise MemoryError("oracle window buffer")
     return out
+
+
+def init_rows(s: np.ndarray, seed: int, start: int, row0: int, nrows: int) -> None:
+    """Start state of rows [row0, row0 + nrows) of the full lattice s (in place)."""
+    assert s.flags.c_contiguous and s.dtype == np.int8
+    lib().oracle_init_rows(_ptr(s, ctypes.c_int8), s.shape[0], int(seed), int(start), int(row0), int(nrows))
+
+
+def half_sweep_rows(s: np.ndarray, c: int, beta: float, seed: int, sweep: int, row0: int, nrows: int) -> int:
+    """Colour-c half-sweep of rows [row0, row0 + nrows) only (timing samples)."""
+    assert s.flags.c_contiguous and s.dtype == np.int8
+    return int(lib().oracle_half_sweep_rows(_ptr(s, ctypes.c_int8), s.shape[0], int(c), float(beta), int(seed),
+                                            int(sweep), int(row0), int(nrows)))
 
 
 def lattice_hash(s: np.ndarray) -> str:

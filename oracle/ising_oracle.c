@@ -282,3 +282,59 @@ ORACLE_API int oracle_window(int64_t L, double beta, uint64_t seed, int start, i
     free(buf);
     return 0;
 }
+
+/* ---------------------------------------------------------------------------
+ * Row-band forms, used only to time a bounded sample of a large lattice on the
+ * host (the CPU baseline): the start state and the half-sweep of rows
+ * [row0, row0 + nrows) of the full L x L lattice, with the same per-site rule,
+ * keying and Philox as above.  The neighbour rows row0 - 1 and row0 + nrows are
+ * read from s and must have been initialised by the caller.
+ * ------------------------------------------------------------------------- */
+ORACLE_API void oracle_init_rows(int8_t *s, int64_t L, uint64_t seed, int start, int64_t row0, int64_t nrows)
+{
+#pragma omp parallel for schedule(static)
+    for (int64_t a = 0; a < nrows; ++a) {
+        int64_t i = wrap(row0 + a, L);
+        for (int64_t j = 0; j < L; ++j) {
+            if (start == 1) {
+                s[i * L + j] = 1;
+            } else {
+                uint32_t x = site_word(L, i, j, seed, 0xFFFFFFFFu, (int)((i + j) & 1));
+                s[i * L + j] = (x < 0x80000000u) ? 1 : -1;
+            }
+        }
+    }
+}
+
+ORACLE_API int64_t oracle_half_sweep_rows(int8_t *s, int64_t L, int c, double beta, uint64_t seed, uint32_t sweep,
+                                          int64_t row0, int64_t nrows)
+{
+    uint64_t T[2];
+    oracle_thresholds(beta, T);
+    int64_t dE = 0;
+#pragma omp parallel for reduction(+ : dE) schedule(static)
+    for (int64_t a = 0; a < nrows; ++a) {
+        int64_t i = wrap(row0 + a, L);
+        uint64_t cached_q = UINT64_MAX;
+        uint32_t cached[4] = {0, 0, 0, 0};
+        for (int64_t j = 0; j < L; ++j) {
+            if (((i + j) & 1) != c) continue;
+            int nn = s[wrap(i - 1, L) * L + j] + s[wrap(i + 1, L) * L + j]
+                   + s[i * L + wrap(j - 1, L)] + s[i * L + wrap(j + 1, L)];
+            int h = s[i * L + j] * nn;
+            uint64_t p = (uint64_t)i * (uint64_t)(L / 2) + (uint64_t)(j >> 1);
+            uint64_t q = p >> 2;
+            if (q != cached_q) {
+                uint32_t ctr[4] = {(uint32_t)q, (uint32_t)(q >> 32), sweep, (uint32_t)c};
+                uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+                oracle_philox4x32_10(ctr, key, cached);
+                cached_q = q;
+            }
+            if (oracle_accept(h, cached[p & 3], T[0], T[1])) {
+                s[i * L + j] = (int8_t)(-s[i * L + j]);
+                dE += 2 * h;
+            }
+        }
+    }
+    return dE;
+}

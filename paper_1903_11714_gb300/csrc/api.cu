@@ -1,0 +1,1169 @@
+// C ABI (include/ising.h): single-lattice handles, batches, checkpoints, the
+// tile autotuner and device building blocks.  Host code only; every step of the
+// sweep runs in the kernels of sweep_packed.cu, sweep_int8.cu, lattice_ops.cu
+// and moments.cu.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "ising.h"
+#include "ising_internal.cuh"
+
+using namespace ising;
+
+namespace {
+
+thread_local std::string t_error;
+
+int fail(int code, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    t_error = buf;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what)
+{
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return fail(ISING_ENOMEM, "%s: %s", what, cudaGetErrorString(e));
+    }
+    return fail(ISING_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(call)                                               \
+    do {                                                       \
+        cudaError_t e_ = (call);                               \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);    \
+    } while (0)
+
+constexpr int64_t kPackedMaxL = 1 << 20;
+constexpr int64_t kInt8MaxL = 1 << 17;
+constexpr uint32_t kNoTarget = 0xFFFFFFFFu;
+constexpr int64_t kMaxSweeps = 0xFFFFFFFEll;  // sweep counter is a 32-bit Philox counter word
+constexpr int64_t kStageCapBytes = 100 * 1024;  // per pipeline stage (two stages per CTA)
+
+// Acceptance thresholds T_h = min(2^32, ceil(exp(-2 beta h) 2^32)), h = 2, 4.
+bool thresholds(double beta, uint64_t T[2])
+{
+    if (!std::isfinite(beta) || beta < 0.0) return false;
+    for (int k = 0; k < 2; ++k) {
+        const double p = std::exp(-2.0 * beta * (double)(2 * (k + 1)));
+        double t = std::ceil(p * 4294967296.0);
+        if (t > 4294967296.0) t = 4294967296.0;
+        T[k] = (uint64_t)t;
+    }
+    return true;
+}
+
+void set_thresholds(LatticeDesc& d, const uint64_t T[2])
+{
+    d.t2 = T[0] >= 4294967296ull ? 0xFFFFFFFFu : (uint32_t)T[0];
+    d.t4 = T[1] >= 4294967296ull ? 0xFFFFFFFFu : (uint32_t)T[1];
+    d.all2 = T[0] >= 4294967296ull ? 0xFFFFFFFFu : 0u;
+    d.all4 = T[1] >= 4294967296ull ? 0xFFFFFFFFu : 0u;
+}
+
+int halo_rows_for(int64_t W) { return (W % 4 == 0) ? 1 : 4; }
+
+int64_t stage_bytes_for(int64_t L, int tile_rows)
+{
+    const int64_t W = L / 64;
+    const int64_t words = stage_words((int32_t)W, tile_rows, halo_rows_for(W));
+    return (words * 4 + 15) / 16 * 16;
+}
+
+bool tile_rows_ok(int64_t L, int tr)
+{
+    return (tr == 4 || tr == 8 || tr == 16 || tr == 32 || tr == 64) && tr <= L && L % tr == 0 &&
+           stage_bytes_for(L, tr) <= kStageCapBytes;
+}
+
+// Built-in tile height: about 4096 words per tile, clamped to [4, 64].
+int default_tile_rows(int64_t L)
+{
+    const int64_t W = L / 64;
+    int tr = 64;
+    while (tr > 4 && (int64_t)tr * W > 4096) tr >>= 1;
+    while (tr > 4 && !tile_rows_ok(L, tr)) tr >>= 1;
+    return tr;
+}
+
+// ---------------------------------------------------------------- engine
+// The launch state of the packed persistent kernel: descriptor array, tile
+// table, status word, grid, and an optional captured graph of k sweeps.
+struct Engine {
+    cudaStream_t stream = nullptr;
+    int threads = 256;
+    int grid = 0;
+    int stage_bytes = 0;
+    int max_count = 0;
+    LatticeDesc* d_desc = nullptr;
+    int32_t* d_tile_start = nullptr;
+    int32_t* d_count = nullptr;
+    int* d_status = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    int g_sweeps = 0;
+
+    int setup(int max_count_, int stage_bytes_, int threads_, cudaStream_t s)
+    {
+        max_count = max_count_;
+        stage_bytes = (stage_bytes_ + 15) / 16 * 16;
+        threads = threads_;
+        stream = s;
+        CK(cudaMalloc(&d_desc, sizeof(LatticeDesc) * (size_t)max_count));
+        CK(cudaMalloc(&d_tile_start, sizeof(int32_t) * (size_t)(max_count + 1)));
+        CK(cudaMalloc(&d_count, sizeof(int32_t)));
+        CK(cudaMalloc(&d_status, sizeof(int)));
+        CK(cudaMemsetAsync(d_desc, 0, sizeof(LatticeDesc) * (size_t)max_count, stream));
+        CK(cudaMemsetAsync(d_tile_start, 0, sizeof(int32_t) * (size_t)(max_count + 1), stream));
+        CK(cudaMemsetAsync(d_count, 0, sizeof(int32_t), stream));
+        CK(cudaMemsetAsync(d_status, 0, sizeof(int), stream));
+        return configure();
+    }
+
+    int configure()
+    {
+        const size_t smem = (size_t)packed_smem_header_bytes(threads) + 2 * (size_t)stage_bytes;
+        CK(packed_set_smem_limit(threads, smem));
+        int per_sm = 0;
+        CK(packed_occupancy(threads, smem, &per_sm));
+        if (per_sm < 1) return fail(ISING_EINVAL, "sweep kernel does not fit: %d threads, %zu B smem", threads, smem);
+        grid = per_sm * sm_count();
+        drop_graph();
+        return ISING_OK;
+    }
+
+    void drop_graph()
+    {
+        if (gexec) cudaGraphExecDestroy(gexec);
+        gexec = nullptr;
+        g_sweeps = 0;
+    }
+
+    int upload_desc(int idx, const LatticeDesc& d)
+    {
+        CK(cudaMemcpyAsync(d_desc + idx, &d, sizeof(LatticeDesc), cudaMemcpyHostToDevice, stream));
+        return ISING_OK;
+    }
+
+    int upload_tiles(const std::vector<int32_t>& tile_start, int32_t count)
+    {
+        CK(cudaMemcpyAsync(d_tile_start, tile_start.data(), sizeof(int32_t) * tile_start.size(),
+                           cudaMemcpyHostToDevice, stream));
+        CK(cudaMemcpyAsync(d_count, &count, sizeof(int32_t), cudaMemcpyHostToDevice, stream));
+        // pageable source: make sure the driver has consumed it before the vector changes
+        CK(cudaStreamSynchronize(stream));
+        return ISING_OK;
+    }
+
+    TileTable table() const
+    {
+        TileTable tt;
+        tt.desc = d_desc;
+        tt.tile_start = d_tile_start;
+        tt.count = d_count;
+        return tt;
+    }
+
+    int enqueue_sweeps(int64_t n)
+    {
+        const TileTable tt = table();
+        for (int64_t k = 0; k < n; ++k) {
+            for (int c = 0; c < 2; ++c) {
+                cudaError_t e = launch_packed_half_sweep(tt, c, (int)k, d_status, grid, threads, stage_bytes, stream);
+                if (e != cudaSuccess) return cuda_fail(e, "packed half-sweep launch");
+            }
+        }
+        cudaError_t e = launch_packed_advance(d_desc, d_count, max_count, (int)n, stream);
+        if (e != cudaSuccess) return cuda_fail(e, "advance launch");
+        return ISING_OK;
+    }
+
+    int run(int64_t sweeps, int graph_sweeps)
+    {
+        if (sweeps == 0) return ISING_OK;
+        if (graph_sweeps <= 0) return enqueue_sweeps(sweeps);
+        if (sweeps % graph_sweeps) return fail(ISING_EINVAL, "sweeps %lld not a multiple of graph_sweeps %d",
+                                               (long long)sweeps, graph_sweeps);
+        if (!gexec || g_sweeps != graph_sweeps) {
+            drop_graph();
+            CK(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
+            int rc = enqueue_sweeps(graph_sweeps);
+            cudaGraph_t g = nullptr;
+            cudaError_t e = cudaStreamEndCapture(stream, &g);
+            if (rc != ISING_OK) {
+                if (g) cudaGraphDestroy(g);
+                return rc;
+            }
+            if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+            e = cudaGraphInstantiate(&gexec, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+            g_sweeps = graph_sweeps;
+        }
+        for (int64_t r = 0; r < sweeps / graph_sweeps; ++r) CK(cudaGraphLaunch(gexec, stream));
+        return ISING_OK;
+    }
+
+    int check_status()
+    {
+        int st = 0;
+        CK(cudaMemcpyAsync(&st, d_status, sizeof(int), cudaMemcpyDeviceToHost, stream));
+        CK(cudaStreamSynchronize(stream));
+        if (st != kStatusOk) {
+            CK(cudaMemsetAsync(d_status, 0, sizeof(int), stream));
+            return fail(ISING_ETIMEOUT, "sweep kernel reported status %d (bounded wait expired)", st);
+        }
+        return ISING_OK;
+    }
+
+    void destroy()
+    {
+        drop_graph();
+        cudaFree(d_desc);
+        cudaFree(d_tile_start);
+        cudaFree(d_count);
+        cudaFree(d_status);
+        d_desc = nullptr;
+        d_tile_start = nullptr;
+        d_count = nullptr;
+        d_status = nullptr;
+    }
+};
+
+int make_stream(void* user, cudaStream_t* s, bool* own)
+{
+    if (user) {
+        *s = (cudaStream_t)user;
+        *own = false;
+        return ISING_OK;
+    }
+    CK(cudaStreamCreateWithFlags(s, cudaStreamNonBlocking));
+    *own = true;
+    return ISING_OK;
+}
+
+// ---------------------------------------------------------------- arena
+// First-fit sub-allocator over one device region: the batch's HBM budget.
+struct Arena {
+    char* base = nullptr;
+    int64_t size = 0;
+    int64_t used = 0;
+    std::map<int64_t, int64_t> free_;  // offset -> length
+
+    int init(int64_t bytes)
+    {
+        size = (bytes + 255) / 256 * 256;
+        CK(cudaMalloc(&base, (size_t)size));
+        free_.clear();
+        free_[0] = size;
+        used = 0;
+        return ISING_OK;
+    }
+    int64_t alloc(int64_t bytes)
+    {
+        bytes = (bytes + 255) / 256 * 256;
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second >= bytes) {
+                const int64_t off = it->first, len = it->second;
+                free_.erase(it);
+                if (len > bytes) free_[off + bytes] = len - bytes;
+                used += bytes;
+                return off;
+            }
+        }
+        return -1;
+    }
+    void release(int64_t off, int64_t bytes)
+    {
+        bytes = (bytes + 255) / 256 * 256;
+        used -= bytes;
+        auto it = free_.emplace(off, bytes).first;
+        auto nx = std::next(it);
+        if (nx != free_.end() && it->first + it->second == nx->first) {
+            it->second += nx->second;
+            free_.erase(nx);
+        }
+        if (it != free_.begin()) {
+            auto pv = std::prev(it);
+            if (pv->first + pv->second == it->first) {
+                pv->second += it->second;
+                free_.erase(it);
+            }
+        }
+    }
+    void destroy()
+    {
+        cudaFree(base);
+        base = nullptr;
+    }
+};
+
+}  // namespace
+
+// ====================================================================== handles
+struct ising_s {
+    int64_t L = 0;
+    double beta = 0;
+    uint64_t seed = 0;
+    int start = 0;
+    int kernel = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    uint64_t T[2] = {0, 0};
+    Engine eng;          // packed
+    LatticeDesc desc{};  // host mirror (packed)
+    uint32_t* planes = nullptr;
+    int8_t* lat = nullptr;  // int8
+    int64_t* hist = nullptr;
+    int64_t hist_cap = 0;
+    int64_t sweeps_done = 0;
+    int64_t* d_me0 = nullptr;   // start-state (M, E)
+    double* d_mom = nullptr;    // 6 doubles
+    uint64_t* d_sums = nullptr; // 11 limbs
+};
+
+struct ising_batch_s {
+    struct Slot {
+        bool used = false;
+        int64_t L = 0;
+        int64_t off = 0, bytes = 0;
+        int64_t sweeps_cap = 0;
+        LatticeDesc desc{};
+    };
+    int capacity = 0;
+    int64_t max_L = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    Engine eng;
+    Arena arena;
+    std::vector<Slot> slots;
+    int32_t count = 0;
+    int64_t* d_me = nullptr;
+    double* d_mom = nullptr;
+    uint64_t* d_sums = nullptr;
+};
+
+namespace {
+
+int ensure_hist(ising_t h, int64_t need)
+{
+    if (need <= h->hist_cap) return ISING_OK;
+    int64_t cap = h->hist_cap ? h->hist_cap : 1024;
+    while (cap < need) cap *= 2;
+    int64_t* nh = nullptr;
+    CK(cudaMalloc(&nh, sizeof(int64_t) * 2 * (size_t)cap));
+    if (h->hist && h->sweeps_done)
+        CK(cudaMemcpyAsync(nh, h->hist, sizeof(int64_t) * 2 * (size_t)h->sweeps_done, cudaMemcpyDeviceToDevice,
+                           h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    cudaFree(h->hist);
+    h->hist = nh;
+    h->hist_cap = cap;
+    if (h->kernel == ISING_PACKED) {
+        h->desc.hist = nh;
+        h->desc.sweep = (uint32_t)h->sweeps_done;
+        int rc = h->eng.upload_desc(0, h->desc);
+        if (rc) return rc;
+    }
+    return ISING_OK;
+}
+
+int check_handle(ising_t h)
+{
+    if (!h) return fail(ISING_EINVAL, "null handle");
+    return ISING_OK;
+}
+
+int read_status(ising_t h)
+{
+    if (h->kernel == ISING_PACKED) return h->eng.check_status();
+    CK(cudaStreamSynchronize(h->stream));
+    return ISING_OK;
+}
+
+// Copies the lattice to host int8 through a bounded device staging buffer.
+int packed_to_host(const uint32_t* black, const uint32_t* white, int64_t L, int8_t* out, cudaStream_t s)
+{
+    const int64_t rows_per = std::max<int64_t>(1, (int64_t)(256ll << 20) / L);
+    const int64_t chunk_rows = std::min<int64_t>(L, rows_per);
+    int8_t* tmp = nullptr;
+    CK(cudaMalloc(&tmp, (size_t)(chunk_rows * L)));
+    for (int64_t r0 = 0; r0 < L; r0 += chunk_rows) {
+        const int64_t nr = std::min<int64_t>(chunk_rows, L - r0);
+        cudaError_t e = launch_unpack(black, white, tmp, L, r0, nr, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(out + r0 * L, tmp, (size_t)(nr * L), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) {
+            cudaFree(tmp);
+            return cuda_fail(e, "unpack to host");
+        }
+    }
+    cudaFree(tmp);
+    return ISING_OK;
+}
+
+int host_to_packed(const int8_t* in, uint32_t* black, uint32_t* white, int64_t L, cudaStream_t s)
+{
+    const int64_t rows_per = std::max<int64_t>(1, (int64_t)(256ll << 20) / L);
+    const int64_t chunk_rows = std::min<int64_t>(L, rows_per);
+    int8_t* tmp = nullptr;
+    CK(cudaMalloc(&tmp, (size_t)(chunk_rows * L)));
+    for (int64_t r0 = 0; r0 < L; r0 += chunk_rows) {
+        const int64_t nr = std::min<int64_t>(chunk_rows, L - r0);
+        cudaError_t e = cudaMemcpyAsync(tmp, in + r0 * L, (size_t)(nr * L), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = launch_pack(tmp, black, white, L, r0, nr, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) {
+            cudaFree(tmp);
+            return cuda_fail(e, "pack from host");
+        }
+    }
+    cudaFree(tmp);
+    return ISING_OK;
+}
+
+bool spins_valid(const int8_t* in, int64_t n)
+{
+    for (int64_t k = 0; k < n; ++k)
+        if (in[k] != 1 && in[k] != -1) return false;
+    return true;
+}
+
+int refresh_me0(ising_t h)
+{
+    cudaError_t e;
+    if (h->kernel == ISING_PACKED)
+        e = launch_packed_observe(h->planes, h->planes + h->L * (h->L / 64), h->L, h->d_me0, h->stream);
+    else
+        e = launch_int8_observe(h->lat, h->L, h->d_me0, h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "observe launch");
+    return ISING_OK;
+}
+
+void destroy_handle(ising_t h)
+{
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    h->eng.destroy();
+    cudaFree(h->planes);
+    cudaFree(h->lat);
+    cudaFree(h->hist);
+    cudaFree(h->d_me0);
+    cudaFree(h->d_mom);
+    cudaFree(h->d_sums);
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    delete h;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* ising_last_error(void) { return t_error.c_str(); }
+
+const char* ising_version(void) { return "ising-gb300 0.1 (sm_103a)"; }
+
+int ising_thresholds(double beta, uint64_t T[2])
+{
+    if (!T) return fail(ISING_EINVAL, "null output");
+    uint64_t t[2];
+    if (!thresholds(beta, t)) return fail(ISING_EINVAL, "beta must be finite and >= 0");
+    T[0] = t[0];
+    T[1] = t[1];
+    return ISING_OK;
+}
+
+int ising_init_ex(ising_t* out, int64_t L, double beta, uint64_t seed, int start, int kernel, void* stream)
+{
+    if (!out) return fail(ISING_EINVAL, "null output");
+    uint64_t T[2];
+    if (!thresholds(beta, T)) return fail(ISING_EINVAL, "beta must be finite and >= 0");
+    if (start != ISING_HOT && start != ISING_COLD) return fail(ISING_EINVAL, "start must be ISING_HOT or ISING_COLD");
+    if (kernel == ISING_PACKED) {
+        if (L < 64 || L % 64 || L > kPackedMaxL)
+            return fail(ISING_EINVAL, "packed kernel needs L %% 64 == 0 and 64 <= L <= %lld", (long long)kPackedMaxL);
+    } else if (kernel == ISING_INT8) {
+        if (L < 8 || L % 8 || L > kInt8MaxL)
+            return fail(ISING_EINVAL, "int8 kernel needs L %% 8 == 0 and 8 <= L <= %lld", (long long)kInt8MaxL);
+    } else {
+        return fail(ISING_EINVAL, "kernel must be ISING_PACKED or ISING_INT8");
+    }
+    ising_t h = new ising_s();
+    h->L = L;
+    h->beta = beta;
+    h->seed = seed;
+    h->start = start;
+    h->kernel = kernel;
+    h->T[0] = T[0];
+    h->T[1] = T[1];
+    int rc = make_stream(stream, &h->stream, &h->own_stream);
+    if (rc) {
+        delete h;
+        return rc;
+    }
+#define CKH(call)                                 \
+    do {                                          \
+        cudaError_t e_ = (call);                  \
+        if (e_ != cudaSuccess) {                  \
+            int r_ = cuda_fail(e_, #call);        \
+            destroy_handle(h);                    \
+            return r_;                            \
+        }                                         \
+    } while (0)
+    CKH(cudaMalloc(&h->d_me0, 2 * sizeof(int64_t)));
+    CKH(cudaMalloc(&h->d_mom, 6 * sizeof(double)));
+    CKH(cudaMalloc(&h->d_sums, 11 * sizeof(uint64_t)));
+    if (kernel == ISING_PACKED) {
+        const int64_t plane_words = L * (L / 64);
+        CKH(cudaMalloc(&h->planes, sizeof(uint32_t) * 2 * (size_t)plane_words));
+        CKH(launch_packed_init(h->planes, h->planes + plane_words, L, seed, start, h->stream));
+        const int tr = default_tile_rows(L);
+        LatticeDesc& d = h->desc;
+        d.plane[0] = h->planes;
+        d.plane[1] = h->planes + plane_words;
+        d.hist = nullptr;
+        d.key = seed;
+        d.L = (int32_t)L;
+        d.W = (int32_t)(L / 64);
+        set_thresholds(d, T);
+        d.tile_rows = tr;
+        d.halo_rows = halo_rows_for(L / 64);
+        d.sweep = 0;
+        d.target = kNoTarget;
+        d.active = 1;
+        rc = h->eng.setup(1, (int)stage_bytes_for(L, tr), 256, h->stream);
+        if (rc) {
+            destroy_handle(h);
+            return rc;
+        }
+        std::vector<int32_t> ts = {0, (int32_t)(L / tr)};
+        rc = h->eng.upload_tiles(ts, 1);
+        if (!rc) rc = ensure_hist(h, 1024);
+        if (rc) {
+            destroy_handle(h);
+            return rc;
+        }
+    } else {
+        CKH(cudaMalloc(&h->lat, (size_t)(L * L)));
+        CKH(launch_int8_init(h->lat, L, seed, start, h->stream));
+        rc = ensure_hist(h, 1024);
+        if (rc) {
+            destroy_handle(h);
+            return rc;
+        }
+    }
+#undef CKH
+    rc = refresh_me0(h);
+    if (!rc) {
+        cudaError_t e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) rc = cuda_fail(e, "init");
+    }
+    if (rc) {
+        destroy_handle(h);
+        return rc;
+    }
+    *out = h;
+    return ISING_OK;
+}
+
+int ising_init(ising_t* out, int64_t L, double beta, uint64_t seed)
+{
+    return ising_init_ex(out, L, beta, seed, ISING_HOT, ISING_PACKED, nullptr);
+}
+
+int ising_sweep(ising_t h, int64_t n)
+{
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (n < 0) return fail(ISING_EINVAL, "n must be >= 0");
+    if (h->sweeps_done + n > kMaxSweeps) return fail(ISING_EINVAL, "sweep counter would pass 2^32 - 2");
+    if (n == 0) return ISING_OK;
+    rc = ensure_hist(h, h->sweeps_done + n);
+    if (rc) return rc;
+    if (h->kernel == ISING_PACKED) {
+        rc = h->eng.run(n, 0);
+        if (rc) return rc;
+    } else {
+        uint32_t t2, t4, all2, all4;
+        LatticeDesc tmp{};
+        set_thresholds(tmp, h->T);
+        t2 = tmp.t2;
+        t4 = tmp.t4;
+        all2 = tmp.all2;
+        all4 = tmp.all4;
+        for (int64_t k = 0; k < n; ++k) {
+            const int64_t s = h->sweeps_done + k;
+            for (int c = 0; c < 2; ++c) {
+                cudaError_t e = launch_int8_half_sweep(h->lat, h->L, h->seed, t2, t4, all2, all4, (uint32_t)s, c,
+                                                       h->hist + 2 * s, h->stream);
+                if (e != cudaSuccess) return cuda_fail(e, "int8 half-sweep launch");
+            }
+        }
+    }
+    h->sweeps_done += n;
+    h->desc.sweep = (uint32_t)h->sweeps_done;
+    return ISING_OK;
+}
+
+int ising_synchronize(ising_t h)
+{
+    int rc = check_handle(h);
+    if (rc) return rc;
+    return read_status(h);
+}
+
+int ising_observables(ising_t h, int64_t* M, int64_t* E, int64_t* sweeps_done)
+{
+    int rc = check_handle(h);
+    if (rc) return rc;
+    int64_t me[2];
+    const int64_t* src = h->sweeps_done ? h->hist + 2 * (h->sweeps_done - 1) : h->d_me0;
+    CK(cudaMemcpyAsync(me, src, sizeof(me), cudaMemcpyDeviceToHost, h->stream));
+    rc = read_status(h);
+    if (rc) return rc;
+    if (M) *M = me[0];
+    if (E) *E = me[1];
+    if (sweeps_done) *sweeps_done = h->sweeps_done;
+    return ISING_OK;
+}
+
+int ising_history(ising_t h, int64_t first, int64_t count, int64_t* M, int64_t* E)
+{
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (first < 0 || count < 0 || first + count > h->sweeps_done)
+        return fail(ISING_EINVAL, "history range [%lld, %lld) beyond %lld sweeps", (long long)first,
+                    (long long)(first + count), (long long)h->sweeps_done);
+    std::vector<int64_t> buf(2 * (size_t)count);
+    if (count) CK(cudaMemcpyAsync(buf.data(), h->hist + 2 * first, sizeof(int64_t) * buf.size(),
+                                  cudaMemcpyDeviceToHost, h->stream));
+    rc = read_status(h);
+    if (rc) return rc;
+    for (int64_t k = 0; k < count; ++k) {
+        if (M) M[k] = buf[2 * k];
+        if (E) E[k] = buf[2 * k + 1];
+    }
+    return ISING_OK;
+}
+
+int ising_moments(ising_t h, int64_t burn_in, double out[6], uint64_t sums[11])
+{
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (!out) return fail(ISING_EINVAL, "null output");
+    if (burn_in < 0 || burn_in >= h->sweeps_done) return fail(ISING_EINVAL, "no samples after burn-in");
+    CK(launch_moments(h->hist, burn_in, h->sweeps_done - burn_in, h->L * h->L, h->d_mom, h->d_sums, h->stream));
+    double m[6];
+    uint64_t s[11];
+    CK(cudaMemcpyAsync(m, h->d_mom, sizeof(m), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(s, h->d_sums, sizeof(s), cudaMemcpyDeviceToHost, h->stream));
+    rc = read_status(h);
+    if (rc) return rc;
+    memcpy(out, m, sizeof(m));
+    if (sums) memcpy(sums, s, sizeof(s));
+    return ISING_OK;
+}
+
+int ising_get_lattice(ising_t h, int8_t* out)
+{
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (!out) return fail(ISING_EINVAL, "null output");
+    rc = read_status(h);
+    if (rc) return rc;
+    if (h->kernel == ISING_PACKED)
+        return packed_to_host(h->planes, h->planes + h->L * (h->L / 64), h->L, out, h->stream);
+    CK(cudaMemcpyAsync(out, h->lat, (size_t)(h->L * h->L), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return ISING_OK;
+}
+
+int ising_set_lattice(ising_t h, const int8_t* in)
+{
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (!in) return fail(ISING_EINVAL, "null input");
+    if (!spins_valid(in, h->L * h->L)) return fail(ISING_EINVAL, "lattice entries must be +1 or -1");
+    rc = read_status(h);
+    if (rc) return rc;
+    if (h->kernel == ISING_PACKED) {
+        rc = host_to_packed(in, h->planes, h->planes + h->L * (h->L / 64), h->L, h->stream);
+        if (rc) return rc;
+    } else {
+        CK(cudaMemcpyAsync(h->lat, in, (size_t)(h->L * h->L), cudaMemcpyHostToDevice, h->stream));
+    }
+    if (h->sweeps_done == 0) {
+        rc = refresh_me0(h);
+        if (rc) return rc;
+    }
+    CK(cudaStreamSynchronize(h->stream));
+    return ISING_OK;
+}
+
+int ising_get_planes(ising_t h, uint32_t* black, uint32_t* white)
+{
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (h->kernel != ISING_PACKED) return fail(ISING_EINVAL, "not a packed handle");
+    const size_t bytes = sizeof(uint32_t) * (size_t)(h->L * (h->L / 64));
+    if (black) CK(cudaMemcpyAsync(black, h->planes, bytes, cudaMemcpyDeviceToHost, h->stream));
+    if (white) CK(cudaMemcpyAsync(white, h->planes + h->L * (h->L / 64), bytes, cudaMemcpyDeviceToHost, h->stream));
+    return read_status(h);
+}
+
+int ising_set_planes(ising_t h, const uint32_t* black, const uint32_t* white)
+{
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (h->kernel != ISING_PACKED) return fail(ISING_EINVAL, "not a packed handle");
+    if (!black || !white) return fail(ISING_EINVAL, "null input");
+    const size_t bytes = sizeof(uint32_t) * (size_t)(h->L * (h->L / 64));
+    CK(cudaMemcpyAsync(h->planes, black, bytes, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(h->planes + h->L * (h->L / 64), white, bytes, cudaMemcpyHostToDevice, h->stream));
+    if (h->sweeps_done == 0) {
+        rc = refresh_me0(h);
+        if (rc) return rc;
+    }
+    return read_status(h);
+}
+
+// ---------------------------------------------------------------- checkpoint
+namespace {
+struct CkptHeader {
+    char magic[8];
+    int64_t version, L, kernel, start, sweeps_done, lattice_bytes;
+    double beta;
+    uint64_t seed;
+};
+int64_t lattice_bytes(ising_t h)
+{
+    return h->kernel == ISING_PACKED ? (int64_t)sizeof(uint32_t) * 2 * h->L * (h->L / 64) : h->L * h->L;
+}
+}  // namespace
+
+int ising_state_bytes(ising_t h, int64_t* bytes)
+{
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (!bytes) return fail(ISING_EINVAL, "null output");
+    *bytes = (int64_t)sizeof(CkptHeader) + lattice_bytes(h) + 16 * h->sweeps_done + 16;
+    return ISING_OK;
+}
+
+int ising_save(ising_t h, void* buf, int64_t bytes)
+{
+    int rc = check_handle(h);
+    if (rc) return rc;
+    int64_t need = 0;
+    ising_state_bytes(h, &need);
+    if (!buf || bytes < need) return fail(ISING_EINVAL, "checkpoint buffer needs %lld bytes", (long long)need);
+    rc = read_status(h);
+    if (rc) return rc;
+    CkptHeader hd{};
+    memcpy(hd.magic, "ISINGCK1", 8);
+    hd.version = 1;
+    hd.L = h->L;
+    hd.kernel = h->kernel;
+    hd.start = h->start;
+    hd.sweeps_done = h->sweeps_done;
+    hd.lattice_bytes = lattice_bytes(h);
+    hd.beta = h->beta;
+    hd.seed = h->seed;
+    char* p = (char*)buf;
+    memcpy(p, &hd, sizeof(hd));
+    p += sizeof(hd);
+    const void* src = h->kernel == ISING_PACKED ? (const void*)h->planes : (const void*)h->lat;
+    CK(cudaMemcpyAsync(p, src, (size_t)hd.lattice_bytes, cudaMemcpyDeviceToHost, h->stream));
+    p += hd.lattice_bytes;
+    CK(cudaMemcpyAsync(p, h->d_me0, 16, cudaMemcpyDeviceToHost, h->stream));
+    p += 16;
+    if (h->sweeps_done)
+        CK(cudaMemcpyAsync(p, h->hist, (size_t)(16 * h->sweeps_done), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return ISING_OK;
+}
+
+int ising_load(ising_t* out, const void* buf, int64_t bytes, void* stream)
+{
+    if (!out || !buf || bytes < (int64_t)sizeof(CkptHeader)) return fail(ISING_EINVAL, "bad checkpoint buffer");
+    CkptHeader hd;
+    memcpy(&hd, buf, sizeof(hd));
+    if (memcmp(hd.magic, "ISINGCK1", 8) != 0 || hd.version != 1) return fail(ISING_EINVAL, "not a checkpoint");
+    ising_t h = nullptr;
+    int rc = ising_init_ex(&h, hd.L, hd.beta, hd.seed, ISING_COLD, (int)hd.kernel, stream);
+    if (rc) return rc;
+    h->start = (int)hd.start;
+    if (hd.lattice_bytes != lattice_bytes(h) ||
+        bytes < (int64_t)sizeof(CkptHeader) + hd.lattice_bytes + 16 + 16 * hd.sweeps_done) {
+        ising_free(h);
+        return fail(ISING_EINVAL, "checkpoint truncated");
+    }
+    const char* p = (const char*)buf + sizeof(CkptHeader);
+    void* dst = h->kernel == ISING_PACKED ? (void*)h->planes : (void*)h->lat;
+    rc = ensure_hist(h, hd.sweeps_done + 1);
+    cudaError_t e = cudaSuccess;
+    if (!rc) e = cudaMemcpyAsync(dst, p, (size_t)hd.lattice_bytes, cudaMemcpyHostToDevice, h->stream);
+    p += hd.lattice_bytes;
+    if (!rc && e == cudaSuccess) e = cudaMemcpyAsync(h->d_me0, p, 16, cudaMemcpyHostToDevice, h->stream);
+    p += 16;
+    if (!rc && e == cudaSuccess && hd.sweeps_done)
+        e = cudaMemcpyAsync(h->hist, p, (size_t)(16 * hd.sweeps_done), cudaMemcpyHostToDevice, h->stream);
+    if (!rc && e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (!rc && e != cudaSuccess) rc = cuda_fail(e, "checkpoint upload");
+    if (!rc) {
+        h->sweeps_done = hd.sweeps_done;
+        h->desc.sweep = (uint32_t)hd.sweeps_done;
+        if (h->kernel == ISING_PACKED) rc = h->eng.upload_desc(0, h->desc);
+    }
+    if (rc) {
+        ising_free(h);
+        return rc;
+    }
+    *out = h;
+    return ISING_OK;
+}
+
+int ising_free(ising_t h)
+{
+    destroy_handle(h);
+    return ISING_OK;
+}
+
+// ======================================================================= batch
+namespace {
+int rebuild_tiles(ising_batch_t b)
+{
+    int32_t count = 0;
+    for (int k = 0; k < b->capacity; ++k)
+        if (b->slots[k].used) count = k + 1;
+    std::vector<int32_t> ts((size_t)count + 1, 0);
+    for (int k = 0; k < count; ++k) {
+        const auto& s = b->slots[k];
+        ts[k + 1] = ts[k] + (s.used ? (int32_t)(s.L / s.desc.tile_rows) : 0);
+    }
+    b->count = count;
+    return b->eng.upload_tiles(ts, count);
+}
+
+int check_batch(ising_batch_t b, int32_t idx)
+{
+    if (!b) return fail(ISING_EINVAL, "null batch");
+    if (idx < 0 || idx >= b->capacity || !b->slots[idx].used) return fail(ISING_EINVAL, "bad slot %d", idx);
+    return ISING_OK;
+}
+
+int batch_sweeps_done(ising_batch_t b, int32_t idx, int64_t* done)
+{
+    uint32_t sw = 0;
+    CK(cudaMemcpyAsync(&sw, &b->eng.d_desc[idx].sweep, sizeof(uint32_t), cudaMemcpyDeviceToHost, b->stream));
+    int rc = b->eng.check_status();
+    if (rc) return rc;
+    *done = sw;
+    return ISING_OK;
+}
+}  // namespace
+
+int ising_batch_create(ising_batch_t* out, int32_t capacity, int64_t max_L, int64_t arena_bytes, int32_t threads,
+                       void* stream)
+{
+    if (!out) return fail(ISING_EINVAL, "null output");
+    if (capacity < 1 || capacity > (1 << 20)) return fail(ISING_EINVAL, "capacity out of range");
+    if (max_L < 64 || max_L % 64 || max_L > kPackedMaxL) return fail(ISING_EINVAL, "max_L must be a multiple of 64");
+    if (threads == 0) threads = 256;
+    if (threads != 128 && threads != 256 && threads != 512)
+        return fail(ISING_EINVAL, "threads must be 128, 256 or 512");
+    if (arena_bytes < 256) return fail(ISING_EINVAL, "arena too small");
+    ising_batch_t b = new ising_batch_s();
+    b->capacity = capacity;
+    b->max_L = max_L;
+    b->slots.resize((size_t)capacity);
+    int rc = make_stream(stream, &b->stream, &b->own_stream);
+    if (rc) {
+        delete b;
+        return rc;
+    }
+    // stage size: the largest tile any admissible lattice can use
+    int64_t stage = 0;
+    for (int64_t L = 64; L <= max_L; L += 64)
+        for (int tr = 4; tr <= 64; tr *= 2)
+            if (tile_rows_ok(L, tr)) stage = std::max(stage, stage_bytes_for(L, tr));
+    rc = b->eng.setup(capacity, (int)stage, threads, b->stream);
+    if (!rc) rc = b->arena.init(arena_bytes);
+    if (!rc) {
+        cudaError_t e = cudaMalloc(&b->d_me, 2 * sizeof(int64_t));
+        if (e == cudaSuccess) e = cudaMalloc(&b->d_mom, 6 * sizeof(double));
+        if (e == cudaSuccess) e = cudaMalloc(&b->d_sums, 11 * sizeof(uint64_t));
+        if (e != cudaSuccess) rc = cuda_fail(e, "batch buffers");
+    }
+    if (!rc) rc = rebuild_tiles(b);
+    if (rc) {
+        ising_batch_free(b);
+        return rc;
+    }
+    *out = b;
+    return ISING_OK;
+}
+
+int ising_batch_add(ising_batch_t b, int64_t L, double beta, uint64_t seed, int32_t start, int64_t sweeps,
+                    int32_t tile_rows, int32_t* idx)
+{
+    if (!b || !idx) return fail(ISING_EINVAL, "null argument");
+    uint64_t T[2];
+    if (!thresholds(beta, T)) return fail(ISING_EINVAL, "beta must be finite and >= 0");
+    if (L < 64 || L % 64 || L > b->max_L) return fail(ISING_EINVAL, "L must be a multiple of 64 and <= max_L");
+    if (start != ISING_HOT && start != ISING_COLD) return fail(ISING_EINVAL, "bad start");
+    if (sweeps < 1 || sweeps > kMaxSweeps) return fail(ISING_EINVAL, "sweeps out of range");
+    if (tile_rows == 0 || !tile_rows_ok(L, tile_rows)) tile_rows = default_tile_rows(L);
+    int slot = -1;
+    for (int k = 0; k < b->capacity; ++k)
+        if (!b->slots[k].used) {
+            slot = k;
+            break;
+        }
+    if (slot < 0) return fail(ISING_EBUSY, "all %d slots in use", b->capacity);
+    const int64_t plane_words = L * (L / 64);
+    const int64_t plane_bytes = (int64_t)sizeof(uint32_t) * 2 * plane_words;
+    const int64_t bytes = plane_bytes + 16 * sweeps;
+    const int64_t off = b->arena.alloc(bytes);
+    if (off < 0)
+        return fail(ISING_ENOMEM, "arena full: %lld of %lld bytes used, need %lld", (long long)b->arena.used,
+                    (long long)b->arena.size, (long long)bytes);
+    auto& s = b->slots[slot];
+    s.used = true;
+    s.L = L;
+    s.off = off;
+    s.bytes = bytes;
+    s.sweeps_cap = sweeps;
+    uint32_t* planes = reinterpret_cast<uint32_t*>(b->arena.base + off);
+    LatticeDesc& d = s.desc;
+    d = LatticeDesc{};
+    d.plane[0] = planes;
+    d.plane[1] = planes + plane_words;
+    d.hist = reinterpret_cast<int64_t*>(b->arena.base + off + plane_bytes);
+    d.key = seed;
+    d.L = (int32_t)L;
+    d.W = (int32_t)(L / 64);
+    set_thresholds(d, T);
+    d.tile_rows = tile_rows;
+    d.halo_rows = halo_rows_for(L / 64);
+    d.sweep = 0;
+    d.target = (uint32_t)sweeps;
+    d.active = 1;
+    cudaError_t e = launch_packed_init(d.plane[0], d.plane[1], L, seed, start, b->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "init launch");
+    int rc = b->eng.upload_desc(slot, d);
+    if (!rc) rc = rebuild_tiles(b);
+    if (rc) return rc;
+    *idx = slot;
+    return ISING_OK;
+}
+
+int ising_batch_remove(ising_batch_t b, int32_t idx)
+{
+    int rc = check_batch(b, idx);
+    if (rc) return rc;
+    auto& s = b->slots[idx];
+    s.desc.active = 0;
+    rc = b->eng.upload_desc(idx, s.desc);
+    if (rc) return rc;
+    s.used = false;
+    b->arena.release(s.off, s.bytes);
+    return rebuild_tiles(b);
+}
+
+int ising_batch_run(ising_batch_t b, int64_t sweeps, int32_t graph_sweeps)
+{
+    if (!b) return fail(ISING_EINVAL, "null batch");
+    if (sweeps < 0) return fail(ISING_EINVAL, "sweeps must be >= 0");
+    return b->eng.run(sweeps, graph_sweeps);
+}
+
+int ising_batch_sweeps_done(ising_batch_t b, int32_t idx, int64_t* sweeps_done)
+{
+    int rc = check_batch(b, idx);
+    if (rc) return rc;
+    if (!sweeps_done) return fail(ISING_EINVAL, "null output");
+    return batch_sweeps_done(b, idx, sweeps_done);
+}
+
+int ising_batch_observables(ising_batch_t b, int32_t idx, int64_t* M, int64_t* E, int64_t* sweeps_done)
+{
+    int rc = check_batch(b, idx);
+    if (rc) return rc;
+    int64_t done = 0;
+    rc = batch_sweeps_done(b, idx, &done);
+    if (rc) return rc;
+    const auto& d = b->slots[idx].desc;
+    int64_t me[2];
+    if (done == 0) {
+        CK(launch_packed_observe(d.plane[0], d.plane[1], d.L, b->d_me, b->stream));
+        CK(cudaMemcpyAsync(me, b->d_me, sizeof(me), cudaMemcpyDeviceToHost, b->stream));
+    } else {
+        CK(cudaMemcpyAsync(me, d.hist + 2 * (done - 1), sizeof(me), cudaMemcpyDeviceToHost, b->stream));
+    }
+    CK(cudaStreamSynchronize(b->stream));
+    if (M) *M = me[0];
+    if (E) *E = me[1];
+    if (sweeps_done) *sweeps_done = done;
+    return ISING_OK;
+}
+
+int ising_batch_history(ising_batch_t b, int32_t idx, int64_t first, int64_t count, int64_t* M, int64_t* E)
+{
+    int rc = check_batch(b, idx);
+    if (rc) return rc;
+    int64_t done = 0;
+    rc = batch_sweeps_done(b, idx, &done);
+    if (rc) return rc;
+    if (first < 0 || count < 0 || first + count > done) return fail(ISING_EINVAL, "history range beyond sweeps done");
+    std::vector<int64_t> buf(2 * (size_t)count);
+    const auto& d = b->slots[idx].desc;
+    if (count) CK(cudaMemcpyAsync(buf.data(), d.hist + 2 * first, sizeof(int64_t) * buf.size(),
+                                  cudaMemcpyDeviceToHost, b->stream));
+    CK(cudaStreamSynchronize(b->stream));
+    for (int64_t k = 0; k < count; ++k) {
+        if (M) M[k] = buf[2 * k];
+        if (E) E[k] = buf[2 * k + 1];
+    }
+    return ISING_OK;
+}
+
+int ising_batch_moments(ising_batch_t b, int32_t idx, int64_t burn_in, double out[6], uint64_t sums[11])
+{
+    int rc = check_batch(b, idx);
+    if (rc) return rc;
+    if (!out) return fail(ISING_EINVAL, "null output");
+    int64_t done = 0;
+    rc = batch_sweeps_done(b, idx, &done);
+    if (rc) return rc;
+    if (burn_in < 0 || burn_in >= done) return fail(ISING_EINVAL, "no samples after burn-in");
+    const auto& d = b->slots[idx].desc;
+    CK(launch_moments(d.hist, burn_in, done - burn_in, (int64_t)d.L * d.L, b->d_mom, b->d_sums, b->stream));
+    double m[6];
+    uint64_t s[11];
+    CK(cudaMemcpyAsync(m, b->d_mom, sizeof(m), cudaMemcpyDeviceToHost, b->stream));
+    CK(cudaMemcpyAsync(s, b->d_sums, sizeof(s), cudaMemcpyDeviceToHost, b->stream));
+    CK(cudaStreamSynchronize(b->stream));
+    memcpy(out, m, sizeof(m));
+    if (sums) memcpy(sums, s, sizeof(s));
+    return ISING_OK;
+}
+
+int ising_batch_get_lattice(ising_batch_t b, int32_t idx, int8_t* out)
+{
+    int rc = check_batch(b, idx);
+    if (rc) return rc;
+    if (!out) return fail(ISING_EINVAL, "null output");
+    rc = b->eng.check_status();
+    if (rc) return rc;
+    const auto& d = b->slots[idx].desc;
+    return packed_to_host(d.plane[0], d.plane[1], d.L, out, b->stream);
+}
+
+int ising_batch_usage(ising_batch_t b, int64_t* arena_used, int32_t* slots_used)
+{
+    if (!b) return fail(ISING_EINVAL, "null batch");
+    if (arena_used) *arena_used = b->arena.used;
+    if (slots_used) {
+        int32_t n = 0;
+        for (const auto& s : b->slots) n += s.used ? 1 : 0;
+        *slots_used = n;
+    }
+    return ISING_OK;
+}
+
+int ising_batch_synchronize(ising_batch_t b)
+{
+    if (!b) return fail(ISING_EINVAL, "null batch");
+    return b->eng.check_status();
+}
+
+int ising_batch_free(ising_batch_t b)
+{
+    if (!b) return ISING_OK;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    b->eng.destroy();
+    b->arena.destroy();
+    cudaFree(b->d_me);
+    cudaFree(b->d_mom);
+    cudaFree(b->d_sums);
+    if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+    delete b;
+    return ISING_OK;
+}
+
+// ==================================================================== autotune
+int ising_autotune(int64_t L, int32_t* tile_rows, int32_t* threads, double* ms)
+{
+    if (!tile_rows || !threads) return fail(ISING_EINVAL, "null output");
+    if (L < 64 || L % 64 || L > kPackedMaxL) return fail(ISING_EINVAL, "L must be a multiple of 64");
+    double best = 1e300;
+    int best_tr = 0, best_th = 0;
+    const int thread_opts[2] = {256, 512};
+    for (int ti = 0; ti < 2; ++ti) {
+        ising_batch_t b = nullptr;
+        const int64_t arena = (int64_t)sizeof(uint32_t) * 2 * L * (L / 64) + 16 * 64 + 4096;
+        int rc = ising_batch_create(&b, 1, L, arena, thread_opts[ti], nullptr);
+        if (rc) return rc;
+        for (int tr = 4; tr <= 64; tr *= 2) {
+            if (!tile_rows_ok(L, tr)) continue;
+            int32_t idx = -1;
+            rc = ising_batch_add(b, L, 0.4406868, 12345, ISING_HOT, 64, tr, &idx);
+            if (rc) {
+                ising_batch_free(b);
+                return rc;
+            }
+            cudaEvent_t e0, e1;
+            cudaEventCreate(&e0);
+            cudaEventCreate(&e1);
+            rc = b->eng.run(2, 0);  // warm-up
+            const int reps = L >= 8192 ? 4 : 16;
+            cudaEventRecord(e0, b->stream);
+            if (!rc) rc = b->eng.run(reps, 0);
+            cudaEventRecord(e1, b->stream);
+            cudaEventSynchronize(e1);
+            float t = 0;
+            cudaEventElapsedTime(&t, e0, e1);
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            if (!rc) rc = b->eng.check_status();
+            if (rc) {
+                ising_batch_free(b);
+                return rc;
+            }
+            const double per = (double)t / reps;
+            if (per < best) {
+                best = per;
+                best_tr = tr;
+                best_th = thread_opts[ti];
+            }
+            ising_batch_remove(b, idx);
+        }
+        ising_batch_free(b);
+    }
+    *tile_rows = best_tr;
+    *threads = best_th;
+    if (ms) *ms = best;
+    return ISING_OK;
+}
+
+// ============================================================ device blocks
+int ising_dev_philox(uint64_t key, const uint32_t ctr[4], int64_t nblocks, uint32_t* out, void* stream)
+{
+    if (!ctr || !out || nblocks < 0) return fail(ISING_EINVAL, "bad argument");
+    CK(launch_philox_words(key, ctr, nblocks, out, (cudaStream_t)stream));
+    return ISING_OK;
+}
+
+}  // extern "C"

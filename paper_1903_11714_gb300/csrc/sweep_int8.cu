@@ -1,0 +1,180 @@
+// Plain int8 checkerboard half-sweep: the GPU analogue of the paper's
+// UpdateNaive (Algorithm 1) on a row-major L x L lattice of +1/-1 bytes, with
+// the same Philox keying, integer thresholds and fused M/E counts as the
+// bit-packed kernel, so both reach the same chain bit for bit.
+//
+// One thread owns an 8-byte chunk of a row (columns 8g .. 8g+7).  The four
+// target-colour sites in it, j = 8g + 2b + r with r = (i + c) & 1, have plane
+// indices p = i*L/2 + 4g + b and so share one Philox call (q = i*L/8 + g).
+#include "ising_internal.cuh"
+#include "philox.cuh"
+
+namespace ising {
+namespace {
+
+constexpr uint32_t kInitSweep = 0xFFFFFFFFu;
+
+__device__ __forceinline__ int sbyte(uint64_t v, int k)
+{
+    return (int)(int8_t)(uint8_t)(v >> (8 * k));
+}
+
+__global__ void int8_init_kernel(int8_t* lat, int64_t L, uint64_t key, int start)
+{
+    const int64_t G = L / 8;
+    const int64_t chunks = L * G;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < chunks;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = idx / G, g = idx - i * G;
+        uint64_t v = 0;
+        if (start == 1) {
+            v = 0x0101010101010101ull;
+        } else {
+            const uint64_t q = (uint64_t)i * (uint64_t)(L / 8) + (uint64_t)g;
+            for (int c = 0; c < 2; ++c) {
+                uint32_t x[4];
+                philox4x32_10((uint32_t)q, (uint32_t)(q >> 32), kInitSweep, (uint32_t)c, key, x);
+                const int r = (int)((i + c) & 1);
+                for (int b = 0; b < 4; ++b) {
+                    const uint64_t byte = x[b] < 0x80000000u ? 0x01ull : 0xFFull;
+                    v |= byte << (8 * (2 * b + r));
+                }
+            }
+        }
+        *reinterpret_cast<uint64_t*>(lat + i * L + 8 * g) = v;
+    }
+}
+
+__device__ __forceinline__ void block_add_pair(long long a, long long b, int64_t* slot)
+{
+    __shared__ long long red[2][32];
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        b += __shfl_down_sync(0xffffffffu, b, o);
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) {
+        red[0][warp] = a;
+        red[1][warp] = b;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long sa = 0, sb = 0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+            sa += red[0][k];
+            sb += red[1][k];
+        }
+        atomicAdd(reinterpret_cast<unsigned long long*>(slot), (unsigned long long)sa);
+        atomicAdd(reinterpret_cast<unsigned long long*>(slot + 1), (unsigned long long)sb);
+    }
+}
+
+__global__ void int8_half_sweep_kernel(int8_t* lat, int64_t L, uint64_t key, uint32_t t2, uint32_t t4, uint32_t all2,
+                                       uint32_t all4, uint32_t sweep, int colour, int64_t* hist_slot)
+{
+    const int64_t G = L / 8;
+    const int64_t chunks = L * G;
+    if (colour == 0 && blockIdx.x == 0 && threadIdx.x == 0) {
+        hist_slot[0] = 0;  // opened here, filled by the colour-1 pass of the same sweep
+        hist_slot[1] = 0;
+    }
+    long long m_acc = 0, e_acc = 0;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < chunks;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = idx / G, g = idx - i * G;
+        const int64_t iu = i == 0 ? L - 1 : i - 1, id = i + 1 == L ? 0 : i + 1;
+        const int r = (int)((i + colour) & 1);
+        int8_t* row = lat + i * L;
+        const uint64_t cur = *reinterpret_cast<const uint64_t*>(row + 8 * g);
+        const uint64_t upv = *reinterpret_cast<const uint64_t*>(lat + iu * L + 8 * g);
+        const uint64_t dnv = *reinterpret_cast<const uint64_t*>(lat + id * L + 8 * g);
+        // the one neighbour outside the chunk: column 8g-1 (r = 0) or 8g+8 (r = 1)
+        const int64_t edge_col = r ? (g + 1 == G ? 0 : 8 * g + 8) : (g == 0 ? L - 1 : 8 * g - 1);
+        const int edge = row[edge_col];
+
+        const uint64_t q = (uint64_t)i * (uint64_t)(L / 8) + (uint64_t)g;
+        uint32_t x[4];
+        philox4x32_10((uint32_t)q, (uint32_t)(q >> 32), sweep, (uint32_t)colour, key, x);
+
+        uint64_t nv = cur;
+        long long e_here = 0;
+        for (int b = 0; b < 4; ++b) {
+            const int k = 2 * b + r;  // byte of the target site in the chunk
+            const int s = sbyte(cur, k);
+            const int left = k == 0 ? edge : sbyte(cur, k - 1);
+            const int right = k == 7 ? edge : sbyte(cur, k + 1);
+            const int nn = sbyte(upv, k) + sbyte(dnv, k) + left + right;
+            const int h = s * nn;
+            bool acc;
+            if (h <= 0)
+                acc = true;
+            else if (h == 2)
+                acc = all2 || x[b] < t2;
+            else
+                acc = all4 || x[b] < t4;
+            const int snew = acc ? -s : s;
+            if (acc) nv ^= (0xFEull << (8 * k));  // 0x01 <-> 0xFF
+            e_here -= (long long)snew * nn;
+        }
+        if (nv != cur) *reinterpret_cast<uint64_t*>(row + 8 * g) = nv;
+        if (colour == 1) {
+            long long msum = 0;
+            for (int k = 0; k < 8; ++k) msum += sbyte(nv, k);
+            m_acc += msum;
+            e_acc += e_here;
+        }
+    }
+    if (colour == 1) block_add_pair(m_acc, e_acc, hist_slot);
+}
+
+__global__ void int8_observe_kernel(const int8_t* lat, int64_t L, int64_t* ME)
+{
+    long long m_acc = 0, e_acc = 0;
+    const int64_t N = L * L;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < N;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = idx / L, j = idx - i * L;
+        const int s = lat[idx];
+        m_acc += s;
+        e_acc -= (long long)s * (lat[(i + 1 == L ? 0 : i + 1) * L + j] + lat[i * L + (j + 1 == L ? 0 : j + 1)]);
+    }
+    block_add_pair(m_acc, e_acc, ME);
+}
+
+__global__ void zero_pair_kernel(int64_t* p)
+{
+    p[0] = 0;
+    p[1] = 0;
+}
+
+int grid_cap(int64_t work, int threads, int per_sm)
+{
+    const int64_t want = (work + threads - 1) / threads;
+    const int64_t cap = (int64_t)sm_count() * per_sm;
+    return (int)(want < 1 ? 1 : (want > cap ? cap : want));
+}
+
+}  // namespace
+
+cudaError_t launch_int8_init(int8_t* lat, int64_t L, uint64_t key, int start, cudaStream_t s)
+{
+    int8_init_kernel<<<grid_cap(L * (L / 8), 256, 16), 256, 0, s>>>(lat, L, key, start);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_int8_half_sweep(int8_t* lat, int64_t L, uint64_t key, uint32_t t2, uint32_t t4, uint32_t all2,
+                                   uint32_t all4, uint32_t sweep, int colour, int64_t* hist_slot, cudaStream_t s)
+{
+    int8_half_sweep_kernel<<<grid_cap(L * (L / 8), 256, 8), 256, 0, s>>>(lat, L, key, t2, t4, all2, all4, sweep,
+                                                                        colour, hist_slot);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_int8_observe(const int8_t* lat, int64_t L, int64_t* ME, cudaStream_t s)
+{
+    zero_pair_kernel<<<1, 1, 0, s>>>(ME);
+    int8_observe_kernel<<<grid_cap(L * L, 256, 8), 256, 0, s>>>(lat, L, ME);
+    return cudaGetLastError();
+}
+
+}  // namespace ising

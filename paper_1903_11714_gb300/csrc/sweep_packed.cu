@@ -1,0 +1,393 @@
+// Bit-packed checkerboard half-sweep (the paper's UpdateOptim, Algorithm 2, on
+// multi-spin-coded colour planes) with fused magnetisation / energy counts.
+//
+// Layout: two planes (black = colour 0, white = colour 1), L rows of W = L/64
+// 32-bit words each; bit b of word w in row i of plane c is the site
+// (i, j = 2(32w + b) + ((i + c) & 1)), bit 1 = spin +1.
+//
+// Neighbours of a target site (i, 2k + r), r = (i + c) & 1, all in the other
+// plane: (i-1, k), (i+1, k), (i, k), and (i, k-1) when r = 0 or (i, k+1) when
+// r = 1 (torus wrap in both directions).  This is the neighbour topology of the
+// compact sub-lattice formulas in Sec. 3.2, with the boundary compensation of
+// Algorithms 1-2 replaced by halo rows and a wrapped funnel shift.
+//
+// Per 32-site word: n_anti (number of anti-aligned neighbours, 0..4) comes from a
+// bitwise 4-input adder; h = sigma * nn = 4 - 2 n_anti.  h <= 0 flips always;
+// h = 2 flips iff the site's Philox word is below T2, h = 4 iff below T4
+// (Sec. 3.1 acceptance min{1, exp(-2 beta h)} as an integer threshold).
+//
+// Each persistent CTA walks the tile table: a tile is `tile_rows` full rows of
+// one lattice.  Thread 0 stages the tile's source rows (plus the halo rows above
+// and below, wrapped) and target rows into shared memory with bulk async copies
+// (cp.async.bulk, completion on an mbarrier), double-buffered so the next tile
+// lands while the current one is computed.
+#include "ising_internal.cuh"
+#include "philox.cuh"
+
+namespace ising {
+namespace {
+
+constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz: far beyond any copy
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
+{
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+// Bounded wait: returns false after ~kWaitCycles without completion.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (clock64() - t0 > kWaitCycles) return false;
+    }
+    return true;
+}
+
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_mbarrier_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// Lattice owning global tile t (binary search of the prefix table).
+__device__ __forceinline__ int lattice_of_tile(const int32_t* tile_start, int count, int t)
+{
+    int lo = 0, hi = count;  // tile_start[lo] <= t < tile_start[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(tile_start + mid) <= t)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+struct TileInfo {
+    int lat;
+    bool live;
+};
+
+__device__ __forceinline__ TileInfo tile_info(const TileTable& tt, int count, int t, int step)
+{
+    TileInfo ti;
+    ti.lat = lattice_of_tile(tt.tile_start, count, t);
+    const LatticeDesc& d = tt.desc[ti.lat];
+    ti.live = d.active && (d.sweep + (uint32_t)step < d.target);
+    return ti;
+}
+
+// Thread 0: stage the tile's rows.  Source rows [i0 - HB, i0 + TR + HB) (wrapped)
+// and target rows [i0, i0 + TR).  Every copy starts on a 16-byte boundary: with
+// W % 4 == 0 every row does; otherwise HB = 4 and tiles start on rows that are
+// multiples of 4, so each copied block starts at a multiple of 4 rows.
+__device__ __forceinline__ void issue_tile(const LatticeDesc& d, int local_tile, int colour, uint32_t* stage,
+                                           uint64_t* bar)
+{
+    const int W = d.W, L = d.L, TR = d.tile_rows, HB = d.halo_rows;
+    const int i0 = local_tile * TR;
+    const uint32_t* src = d.plane[colour ^ 1];
+    const uint32_t* tgt = d.plane[colour];
+    const uint32_t row_bytes = (uint32_t)W * 4u;
+    int ia = i0 - HB;
+    if (ia < 0) ia += L;
+    int ib = i0 + TR;
+    if (ib >= L) ib -= L;
+    uint32_t* s_src = stage;
+    uint32_t* s_tgt = stage + (size_t)(TR + 2 * HB) * W;
+    mbar_expect_tx(bar, row_bytes * (uint32_t)(2 * HB + 2 * TR));
+    bulk_copy_g2s(s_src, src + (size_t)ia * W, row_bytes * HB, bar);
+    bulk_copy_g2s(s_src + (size_t)HB * W, src + (size_t)i0 * W, row_bytes * TR, bar);
+    bulk_copy_g2s(s_src + (size_t)(HB + TR) * W, src + (size_t)ib * W, row_bytes * HB, bar);
+    bulk_copy_g2s(s_tgt, tgt + (size_t)i0 * W, row_bytes * TR, bar);
+}
+
+// New value of one 32-site target word.
+__device__ __forceinline__ uint32_t update_word(uint32_t t, uint32_t up, uint32_t down, uint32_t same,
+                                                uint32_t hz, uint64_t q0, uint64_t key, uint32_t sweep,
+                                                int colour, uint32_t t2, uint32_t t4, uint32_t all2,
+                                                uint32_t all4)
+{
+    // anti-aligned neighbour bits and their 4-input sum n_anti = 4*b2 + 2*b1 + b0
+    const uint32_t au = t ^ up, ad = t ^ down, as = t ^ same, ah = t ^ hz;
+    const uint32_t s0 = au ^ ad, c0 = au & ad;
+    const uint32_t s1 = as ^ ah, c1 = as & ah;
+    const uint32_t b0 = s0 ^ s1, cc = s0 & s1;
+    const uint32_t b1 = c0 ^ c1 ^ cc;
+    const uint32_t b2 = c0 & c1;
+
+    const PhiloxWordConsts pc = philox_consts(key, (uint32_t)(q0 >> 32), sweep, (uint32_t)colour);
+    const uint32_t qlo = (uint32_t)q0;
+    uint32_t q2 = all2, q4 = all4;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        uint32_t x[4];
+        philox_call(qlo + (uint32_t)j, pc, key, x[0], x[1], x[2], x[3]);
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            q2 |= (x[m] < t2 ? 1u : 0u) << (4 * j + m);
+            q4 |= (x[m] < t4 ? 1u : 0u) << (4 * j + m);
+        }
+    }
+    // n_anti >= 2 (h <= 0): always; n_anti == 1 (h = 2): x < T2; n_anti == 0 (h = 4):
+    // x < T4.  T4 <= T2, so q4 is a subset of q2 and ORing q4 everywhere is exact.
+    const uint32_t flip = b1 | b2 | (b0 & q2) | q4;
+    return t ^ flip;
+}
+
+template <int NT>
+__global__ void __launch_bounds__(NT) packed_half_sweep_kernel(TileTable tt, int colour, int step, int* status,
+                                                               int stage_words_max)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);
+    uint32_t* red = reinterpret_cast<uint32_t*>(smem_raw + 16);  // 2 * NT/32 words
+    uint32_t* stages = reinterpret_cast<uint32_t*>(smem_raw + 128 + ((2 * (NT / 32) * 4 + 127) / 128) * 128);
+    const int tid = threadIdx.x;
+    const int count = *tt.count;
+    const int total = __ldg(tt.tile_start + count);
+
+    if (tid == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        fence_mbarrier_init();
+    }
+    __syncthreads();
+
+    int buf = 0;
+    uint32_t phase0 = 0, phase1 = 0;
+    int t = blockIdx.x;
+    TileInfo cur = {0, false};
+    if (t < total) {
+        cur = tile_info(tt, count, t, step);
+        if (cur.live && tid == 0)
+            issue_tile(tt.desc[cur.lat], t - __ldg(tt.tile_start + cur.lat), colour, stages, &bars[0]);
+    }
+
+    int acc_lat = -1;          // lattice whose M/E counts are being accumulated
+    uint32_t ups = 0, anti = 0;  // per-thread counts (colour-1 pass only)
+
+    auto flush = [&](int lat) {
+        // block reduction of (ups, anti) then one pair of 64-bit atomics
+        const uint32_t u = __reduce_add_sync(0xffffffffu, ups);
+        const uint32_t a = __reduce_add_sync(0xffffffffu, anti);
+        if ((tid & 31) == 0) {
+            red[2 * (tid >> 5)] = u;
+            red[2 * (tid >> 5) + 1] = a;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            unsigned long long su = 0, sa = 0;
+            for (int k = 0; k < NT / 32; ++k) {
+                su += red[2 * k];
+                sa += red[2 * k + 1];
+            }
+            const LatticeDesc& d = tt.desc[lat];
+            int64_t* slot = d.hist + 2 * (int64_t)(d.sweep + (uint32_t)step);
+            atomicAdd(reinterpret_cast<unsigned long long*>(slot), 2ull * su);
+            atomicAdd(reinterpret_cast<unsigned long long*>(slot + 1), 2ull * sa);
+        }
+        __syncthreads();
+        ups = 0;
+        anti = 0;
+    };
+
+    for (; t < total; t += gridDim.x) {
+        const int tn = t + gridDim.x;
+        TileInfo nxt = {0, false};
+        if (tn < total) {
+            nxt = tile_info(tt, count, tn, step);
+            if (nxt.live && tid == 0) {
+                fence_proxy_async_smem();
+                issue_tile(tt.desc[nxt.lat], tn - __ldg(tt.tile_start + nxt.lat), colour,
+                           stages + (size_t)(buf ^ 1) * stage_words_max, &bars[buf ^ 1]);
+            }
+        }
+        if (cur.live) {
+            const LatticeDesc& d = tt.desc[cur.lat];
+            const int local_tile = t - __ldg(tt.tile_start + cur.lat);
+            const uint32_t parity = buf ? phase1 : phase0;
+            bool ok = mbar_wait_bounded(&bars[buf], parity);
+            if (buf)
+                phase1 ^= 1;
+            else
+                phase0 ^= 1;
+            if (!__syncthreads_and(ok)) {
+                if (tid == 0) atomicExch(status, kStatusTimeout);
+                // give copies still in flight a bounded chance to land before exiting
+                if (nxt.live) mbar_wait_bounded(&bars[buf ^ 1], buf ? phase0 : phase1);
+                return;
+            }
+            if (colour == 1 && acc_lat != cur.lat) {
+                if (acc_lat >= 0) flush(acc_lat);
+                acc_lat = cur.lat;
+            }
+            const int W = d.W, L = d.L, TR = d.tile_rows, HB = d.halo_rows;
+            const uint64_t key = d.key;
+            const uint32_t sweep = d.sweep + (uint32_t)step;
+            const uint32_t t2 = d.t2, t4 = d.t4, all2 = d.all2, all4 = d.all4;
+            const int i0 = local_tile * TR;
+            uint32_t* out_plane = d.plane[colour];
+            const uint32_t* s_src = stages + (size_t)buf * stage_words_max;
+            const uint32_t* s_tgt = s_src + (size_t)(TR + 2 * HB) * W;
+            if (colour == 0 && local_tile == 0 && tid == 0) {
+                // open this sweep's (M, E) slot: M = 2 * ups - N, E = 2 * anti - 2N
+                int64_t* slot = d.hist + 2 * (int64_t)sweep;
+                const int64_t N = (int64_t)L * L;
+                slot[0] = -N;
+                slot[1] = -2 * N;
+            }
+            const int nwords = TR * W;
+            for (int idx = tid; idx < nwords; idx += NT) {
+                const int r = idx / W;
+                const int w = idx - r * W;
+                const int i = i0 + r;
+                const uint32_t* srow = s_src + (size_t)(HB + r) * W;
+                const uint32_t up = srow[w - W];
+                const uint32_t down = srow[w + W];
+                const uint32_t same = srow[w];
+                const int par = (i + colour) & 1;
+                uint32_t hz;
+                if (par) {
+                    const uint32_t nextw = srow[(w + 1 == W) ? 0 : w + 1];
+                    hz = __funnelshift_r(same, nextw, 1);
+                } else {
+                    const uint32_t prevw = srow[(w == 0) ? W - 1 : w - 1];
+                    hz = __funnelshift_l(prevw, same, 1);
+                }
+                const uint32_t tw = s_tgt[idx];
+                const uint64_t q0 = (uint64_t)i * (uint64_t)(L >> 3) + 8ull * (uint64_t)w;
+                const uint32_t nw = update_word(tw, up, down, same, hz, q0, key, sweep, colour, t2, t4, all2, all4);
+                out_plane[(size_t)i * W + w] = nw;
+                if (colour == 1) {
+                    ups += __popc(nw) + __popc(same);
+                    anti += __popc(nw ^ up) + __popc(nw ^ down) + __popc(nw ^ same) + __popc(nw ^ hz);
+                }
+            }
+        }
+        __syncthreads();
+        buf ^= 1;
+        cur = nxt;
+    }
+    if (colour == 1 && acc_lat >= 0) flush(acc_lat);
+}
+
+// After `steps` sweeps: advance each live lattice's sweep counter (bounded by its target).
+__global__ void packed_advance_kernel(LatticeDesc* desc, const int32_t* count, int steps)
+{
+    const int n = *count;
+    for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < n; l += gridDim.x * blockDim.x) {
+        LatticeDesc& d = desc[l];
+        if (!d.active) continue;
+        const uint64_t nxt = (uint64_t)d.sweep + (uint64_t)steps;
+        d.sweep = (uint32_t)(nxt < d.target ? nxt : (uint64_t)(d.sweep < d.target ? d.target : d.sweep));
+    }
+}
+
+}  // namespace
+
+int packed_smem_header_bytes(int threads)
+{
+    return 128 + ((2 * (threads / 32) * 4 + 127) / 128) * 128;
+}
+
+cudaError_t launch_packed_half_sweep(const TileTable& tt, int colour, int step, int* status, int grid, int threads,
+                                     int smem_stage_bytes, cudaStream_t s)
+{
+    const int stage_words = smem_stage_bytes / 4;
+    const size_t smem = (size_t)packed_smem_header_bytes(threads) + 2 * (size_t)smem_stage_bytes;
+    switch (threads) {
+    case 128:
+        packed_half_sweep_kernel<128><<<grid, 128, smem, s>>>(tt, colour, step, status, stage_words);
+        break;
+    case 256:
+        packed_half_sweep_kernel<256><<<grid, 256, smem, s>>>(tt, colour, step, status, stage_words);
+        break;
+    case 512:
+        packed_half_sweep_kernel<512><<<grid, 512, smem, s>>>(tt, colour, step, status, stage_words);
+        break;
+    default:
+        return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t packed_set_smem_limit(int threads, size_t bytes)
+{
+    switch (threads) {
+    case 128:
+        return cudaFuncSetAttribute(packed_half_sweep_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)bytes);
+    case 256:
+        return cudaFuncSetAttribute(packed_half_sweep_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)bytes);
+    case 512:
+        return cudaFuncSetAttribute(packed_half_sweep_kernel<512>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)bytes);
+    default:
+        return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t packed_occupancy(int threads, size_t smem, int* blocks_per_sm)
+{
+    switch (threads) {
+    case 128:
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, packed_half_sweep_kernel<128>, 128, smem);
+    case 256:
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, packed_half_sweep_kernel<256>, 256, smem);
+    case 512:
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, packed_half_sweep_kernel<512>, 512, smem);
+    default:
+        return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_packed_advance(LatticeDesc* desc, const int32_t* count, int max_count, int steps, cudaStream_t s)
+{
+    const int threads = 128;
+    const int grid = (max_count + threads - 1) / threads;
+    packed_advance_kernel<<<grid > 0 ? grid : 1, threads, 0, s>>>(desc, count, steps);
+    return cudaGetLastError();
+}
+
+}  // namespace ising

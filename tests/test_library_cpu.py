@@ -1,0 +1,99 @@
+"""Host-side checks of the CUDA library that need no GPU.
+
+* The library builds for sm_103a, loads, and exports every function that
+  include/ising.h declares (and the binding binds exactly those).
+* ising_thresholds (host-only) equals the oracle's independently written
+  thresholds bit for bit (the FP64 libm reading of the acceptance rule).
+* Argument validation rejects bad input before touching the device.
+"""
+import ctypes
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1903_11714_gb300 import build as libbuild
+from paper_1903_11714_gb300 import ising
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "ising.h")
+
+
+def header_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(ising_\w+)\s*\(", text, flags=re.M)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    libbuild.build()
+    return ising.lib()
+
+
+def test_header_declares_the_survey_boundary():
+    names = header_functions()
+    for required in ("ising_init", "ising_sweep", "ising_observables", "ising_history", "ising_moments",
+                     "ising_get_lattice", "ising_set_lattice", "ising_thresholds", "ising_free",
+                     "ising_last_error", "ising_batch_create", "ising_batch_run", "ising_batch_observables"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    out = subprocess.run(["nm", "-D", "--defined-only", libbuild.LIB], capture_output=True, text=True, check=True)
+    exported = set(re.findall(r"\sT\s(ising_\w+)", out.stdout))
+    declared = set(header_functions())
+    assert declared <= exported, declared - exported
+    assert set(ising.EXPORTS) == declared, set(ising.EXPORTS) ^ declared
+    for name in declared:
+        assert hasattr(lib, name)
+
+
+@pytest.mark.parametrize("beta", [0.0, 1e-7, 0.2, 0.35, 0.4406868, 0.44068679350977151, 0.5, 0.6, 1.3, 7.0,
+                                  50.0, 200.0])
+def test_thresholds_match_oracle(lib, beta):
+    assert ising.ising_thresholds(beta) == oracle.thresholds(beta)
+
+
+def test_thresholds_many_betas_match_oracle(lib):
+    rng = np.random.default_rng(1)
+    for beta in rng.uniform(0.0, 3.0, size=2000):
+        assert ising.ising_thresholds(beta) == oracle.thresholds(beta), beta
+
+
+@pytest.mark.parametrize("beta", [-0.1, float("nan"), float("inf")])
+def test_thresholds_reject_bad_beta(lib, beta):
+    with pytest.raises(ising.IsingError) as e:
+        ising.ising_thresholds(beta)
+    assert e.value.code == ising.ISING_EINVAL
+    assert "beta" in ising.last_error()
+
+
+@pytest.mark.parametrize("L,kernel", [(0, ising.PACKED), (96, ising.PACKED), (32, ising.PACKED),
+                                      (12, ising.INT8), (4, ising.INT8), (2**21, ising.PACKED)])
+def test_init_rejects_bad_sizes_before_device_work(lib, L, kernel):
+    with pytest.raises(ising.IsingError) as e:
+        ising.ising_init_ex(L, 0.44, 1, ising.HOT, kernel)
+    assert e.value.code == ising.ISING_EINVAL
+
+
+def test_init_rejects_bad_start_and_kernel(lib):
+    for start, kernel in ((7, ising.PACKED), (ising.HOT, 9)):
+        with pytest.raises(ising.IsingError) as e:
+            ising.ising_init_ex(64, 0.44, 1, start, kernel)
+        assert e.value.code == ising.ISING_EINVAL
+
+
+def test_null_handles_are_rejected(lib):
+    assert lib.ising_sweep(None, 1) == ising.ISING_EINVAL
+    assert lib.ising_free(None) == ising.ISING_OK
+    assert lib.ising_batch_free(None) == ising.ISING_OK
+    M = ctypes.c_int64()
+    assert lib.ising_observables(None, ctypes.byref(M), None, None) == ising.ISING_EINVAL
+
+
+def test_version_string(lib):
+    assert "sm_103a" in lib.ising_version().decode()
