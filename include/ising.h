@@ -231,6 +231,17 @@ int ising_autotune(int64_t L, int32_t *tile_rows, int32_t *threads, double *ms);
 int ising_dev_philox(uint64_t key, const uint32_t ctr[4], int64_t nblocks, uint32_t *out, void *stream);
 
 /*
+ * Failure-detection self-test of the sweep kernel's bounded waits.  Launches one
+ * half-sweep of a 256 x 256 lattice whose tile barriers expect 16 bytes that are
+ * never sent, with each wait bounded by wait_cycles SM clocks (>= 1000), then
+ * writes the status the host read back to *observed (ISING_ETIMEOUT when the
+ * kernel gave up as designed) and runs one normal sweep to show the context is
+ * still usable.  Returns ISING_OK when that sweep succeeded.  No fault, trap or
+ * unbounded wait is involved.  Not part of the paper: a test hook.
+ */
+int ising_selftest_timeout(int64_t wait_cycles, int *observed);
+
+/*
  * Integer-pipe throughput of this GPU, the denominator of the sweep's ALU
  * roofline: out[0] = 32x32->64 multiplies (both halves used, as in a Philox
  * round) per SM per clock; out[1] = ALU ops (3-input XOR, funnel shift) per SM

@@ -1158,6 +1158,28 @@ int ising_autotune(int64_t L, int32_t* tile_rows, int32_t* threads, double* ms)
     return ISING_OK;
 }
 
+// ================================================================ self-test
+int ising_selftest_timeout(int64_t wait_cycles, int* observed)
+{
+    if (!observed || wait_cycles < 1000 || wait_cycles > 4000000000ll) return fail(ISING_EINVAL, "bad argument");
+    ising_t h = nullptr;
+    int rc = ising_init_ex(&h, 256, 0.44, 1, ISING_HOT, ISING_PACKED, nullptr);
+    if (rc) return rc;
+    // every tile barrier of this launch expects 16 bytes that are never sent
+    cudaError_t e = launch_packed_half_sweep(h->eng.table(), 0, 0, h->eng.d_status, h->eng.grid, h->eng.threads,
+                                             h->eng.stage_bytes, h->stream, (long long)wait_cycles, 16u);
+    if (e != cudaSuccess) {
+        ising_free(h);
+        return cuda_fail(e, "self-test launch");
+    }
+    *observed = h->eng.check_status();
+    // the context must still be usable: a normal sweep now completes cleanly
+    rc = ising_sweep(h, 1);
+    if (!rc) rc = ising_synchronize(h);
+    ising_free(h);
+    return rc;
+}
+
 // ============================================================ device blocks
 int ising_dev_philox(uint64_t key, const uint32_t ctr[4], int64_t nblocks, uint32_t* out, void* stream)
 {

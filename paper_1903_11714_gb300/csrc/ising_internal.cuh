@@ -43,9 +43,16 @@ __host__ __device__ inline int64_t stage_words(int32_t W, int32_t tile_rows, int
     return (int64_t)(tile_rows + 2 * halo_rows) * W + (int64_t)tile_rows * W;
 }
 
-// Launchers (return cudaError_t of the launch).
+// Bound on every mbarrier wait of the sweep kernel, in SM clocks (~2 s at 2 GHz,
+// far beyond any tile copy).  After it the kernel records kStatusTimeout and
+// its CTAs return.
+constexpr long long kWaitLimitCycles = 4000000000LL;
+
+// Launchers (return cudaError_t of the launch).  extra_tx > 0 makes every tile
+// barrier expect bytes that never arrive: only the timeout self-test uses it.
 cudaError_t launch_packed_half_sweep(const TileTable& tt, int colour, int step, int* status, int grid,
-                                     int threads, int smem_stage_bytes, cudaStream_t s);
+                                     int threads, int smem_stage_bytes, cudaStream_t s,
+                                     long long wait_limit = kWaitLimitCycles, uint32_t extra_tx = 0);
 cudaError_t launch_packed_advance(LatticeDesc* desc, const int32_t* count, int max_count, int steps,
                                   cudaStream_t s);
 cudaError_t launch_packed_init(uint32_t* black, uint32_t* white, int64_t L, uint64_t key, int start,

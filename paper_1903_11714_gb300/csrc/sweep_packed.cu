@@ -27,7 +27,6 @@
 namespace ising {
 namespace {
 
-constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz: far beyond any copy
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p)
 {
@@ -58,13 +57,13 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
     return done != 0;
 }
 
-// Bounded wait: returns false after ~kWaitCycles without completion.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity)
+// Bounded wait: returns false after `limit` SM clocks without completion.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, long long limit)
 {
     if (mbar_try_wait(bar, parity)) return true;
     const long long t0 = clock64();
     while (!mbar_try_wait(bar, parity)) {
-        if (clock64() - t0 > kWaitCycles) return false;
+        if (clock64() - t0 > limit) return false;
     }
     return true;
 }
@@ -121,7 +120,7 @@ __device__ __forceinline__ TileInfo tile_info(const TileTable& tt, int count, in
 // W % 4 == 0 every row does; otherwise HB = 4 and tiles start on rows that are
 // multiples of 4, so each copied block starts at a multiple of 4 rows.
 __device__ __forceinline__ void issue_tile(const LatticeDesc& d, int local_tile, int colour, uint32_t* stage,
-                                           uint64_t* bar)
+                                           uint64_t* bar, uint32_t extra_tx)
 {
     const int W = d.W, L = d.L, TR = d.tile_rows, HB = d.halo_rows;
     const int i0 = local_tile * TR;
@@ -134,7 +133,7 @@ __device__ __forceinline__ void issue_tile(const LatticeDesc& d, int local_tile,
     if (ib >= L) ib -= L;
     uint32_t* s_src = stage;
     uint32_t* s_tgt = stage + (size_t)(TR + 2 * HB) * W;
-    mbar_expect_tx(bar, row_bytes * (uint32_t)(2 * HB + 2 * TR));
+    mbar_expect_tx(bar, row_bytes * (uint32_t)(2 * HB + 2 * TR) + extra_tx);
     bulk_copy_g2s(s_src, src + (size_t)ia * W, row_bytes * HB, bar);
     bulk_copy_g2s(s_src + (size_t)HB * W, src + (size_t)i0 * W, row_bytes * TR, bar);
     bulk_copy_g2s(s_src + (size_t)(HB + TR) * W, src + (size_t)ib * W, row_bytes * HB, bar);
@@ -176,7 +175,8 @@ __device__ __forceinline__ uint32_t update_word(uint32_t t, uint32_t up, uint32_
 
 template <int NT>
 __global__ void __launch_bounds__(NT) packed_half_sweep_kernel(TileTable tt, int colour, int step, int* status,
-                                                               int stage_words_max)
+                                                               int stage_words_max, long long wait_limit,
+                                                               uint32_t extra_tx)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);
@@ -200,7 +200,7 @@ __global__ void __launch_bounds__(NT) packed_half_sweep_kernel(TileTable tt, int
     if (t < total) {
         cur = tile_info(tt, count, t, step);
         if (cur.live && tid == 0)
-            issue_tile(tt.desc[cur.lat], t - __ldg(tt.tile_start + cur.lat), colour, stages, &bars[0]);
+            issue_tile(tt.desc[cur.lat], t - __ldg(tt.tile_start + cur.lat), colour, stages, &bars[0], extra_tx);
     }
 
     int acc_lat = -1;          // lattice whose M/E counts are being accumulated
@@ -239,14 +239,14 @@ __global__ void __launch_bounds__(NT) packed_half_sweep_kernel(TileTable tt, int
             if (nxt.live && tid == 0) {
                 fence_proxy_async_smem();
                 issue_tile(tt.desc[nxt.lat], tn - __ldg(tt.tile_start + nxt.lat), colour,
-                           stages + (size_t)(buf ^ 1) * stage_words_max, &bars[buf ^ 1]);
+                           stages + (size_t)(buf ^ 1) * stage_words_max, &bars[buf ^ 1], extra_tx);
             }
         }
         if (cur.live) {
             const LatticeDesc& d = tt.desc[cur.lat];
             const int local_tile = t - __ldg(tt.tile_start + cur.lat);
             const uint32_t parity = buf ? phase1 : phase0;
-            bool ok = mbar_wait_bounded(&bars[buf], parity);
+            bool ok = mbar_wait_bounded(&bars[buf], parity, wait_limit);
             if (buf)
                 phase1 ^= 1;
             else
@@ -254,7 +254,7 @@ __global__ void __launch_bounds__(NT) packed_half_sweep_kernel(TileTable tt, int
             if (!__syncthreads_and(ok)) {
                 if (tid == 0) atomicExch(status, kStatusTimeout);
                 // give copies still in flight a bounded chance to land before exiting
-                if (nxt.live) mbar_wait_bounded(&bars[buf ^ 1], buf ? phase0 : phase1);
+                if (nxt.live) mbar_wait_bounded(&bars[buf ^ 1], buf ? phase0 : phase1, wait_limit);
                 return;
             }
             if (colour == 1 && acc_lat != cur.lat) {
@@ -331,19 +331,19 @@ int packed_smem_header_bytes(int threads)
 }
 
 cudaError_t launch_packed_half_sweep(const TileTable& tt, int colour, int step, int* status, int grid, int threads,
-                                     int smem_stage_bytes, cudaStream_t s)
+                                     int smem_stage_bytes, cudaStream_t s, long long wait_limit, uint32_t extra_tx)
 {
     const int stage_words = smem_stage_bytes / 4;
     const size_t smem = (size_t)packed_smem_header_bytes(threads) + 2 * (size_t)smem_stage_bytes;
     switch (threads) {
     case 128:
-        packed_half_sweep_kernel<128><<<grid, 128, smem, s>>>(tt, colour, step, status, stage_words);
+        packed_half_sweep_kernel<128><<<grid, 128, smem, s>>>(tt, colour, step, status, stage_words, wait_limit, extra_tx);
         break;
     case 256:
-        packed_half_sweep_kernel<256><<<grid, 256, smem, s>>>(tt, colour, step, status, stage_words);
+        packed_half_sweep_kernel<256><<<grid, 256, smem, s>>>(tt, colour, step, status, stage_words, wait_limit, extra_tx);
         break;
     case 512:
-        packed_half_sweep_kernel<512><<<grid, 512, smem, s>>>(tt, colour, step, status, stage_words);
+        packed_half_sweep_kernel<512><<<grid, 512, smem, s>>>(tt, colour, step, status, stage_words, wait_limit, extra_tx);
         break;
     default:
         return cudaErrorInvalidValue;

@@ -65,6 +65,7 @@ _SIGS = {
     "ising_autotune": (ctypes.c_int, [_i64, _P(_i32), _P(_i32), _P(_d)]),
     "ising_dev_philox": (ctypes.c_int, [_u64, _P(ctypes.c_uint32), _i64, _vp, _vp]),
     "ising_probe_int_rates": (ctypes.c_int, [_P(_d)]),
+    "ising_selftest_timeout": (ctypes.c_int, [_i64, _P(ctypes.c_int)]),
 }
 EXPORTS = tuple(_SIGS)
 
@@ -241,6 +242,13 @@ def ising_probe_int_rates() -> tuple[float, float]:
     out = np.zeros(2, dtype=np.float64)
     _check(lib().ising_probe_int_rates(_ptr(out, ctypes.c_double)))
     return float(out[0]), float(out[1])
+
+
+def ising_selftest_timeout(wait_cycles: int) -> int:
+    """Runs the bounded-wait self-test; returns the status the kernel reported."""
+    obs = ctypes.c_int()
+    _check(lib().ising_selftest_timeout(int(wait_cycles), ctypes.byref(obs)))
+    return obs.value
 
 
 # ------------------------------------------------------------------ classes
