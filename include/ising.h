@@ -197,6 +197,18 @@ int ising_batch_run(ising_batch_t b, int64_t sweeps, int32_t graph_sweeps);
 /* Per-lattice sweeps done (synchronises). */
 int ising_batch_sweeps_done(ising_batch_t b, int32_t idx, int64_t *sweeps_done);
 
+/*
+ * Sweeps done of slots 0 .. n-1 in one device-to-host copy (-1 for a free
+ * slot); n <= capacity.  Synchronises.
+ */
+int ising_batch_progress(ising_batch_t b, int64_t *sweeps_done, int32_t n);
+
+/*
+ * Slot idx: current M and E (the start state before any sweep) and sweeps done;
+ * history entries first .. first+count-1; Sec. 4.1 moments over samples
+ * burn_in .. sweeps_done-1 (as ising_moments); the lattice as L*L int8 +1/-1.
+ * All synchronise.
+ */
 int ising_batch_observables(ising_batch_t b, int32_t idx, int64_t *M, int64_t *E, int64_t *sweeps_done);
 int ising_batch_history(ising_batch_t b, int32_t idx, int64_t first, int64_t count, int64_t *M, int64_t *E);
 int ising_batch_moments(ising_batch_t b, int32_t idx, int64_t burn_in, double out[6], uint64_t sums[11]);

@@ -997,6 +997,18 @@ int ising_batch_sweeps_done(ising_batch_t b, int32_t idx, int64_t* sweeps_done)
     return batch_sweeps_done(b, idx, sweeps_done);
 }
 
+int ising_batch_progress(ising_batch_t b, int64_t* sweeps_done, int32_t n)
+{
+    if (!b || !sweeps_done || n < 0 || n > b->capacity) return fail(ISING_EINVAL, "bad argument");
+    std::vector<LatticeDesc> d((size_t)std::max(n, 1));
+    if (n) CK(cudaMemcpyAsync(d.data(), b->eng.d_desc, sizeof(LatticeDesc) * (size_t)n, cudaMemcpyDeviceToHost,
+                              b->stream));
+    int rc = b->eng.check_status();
+    if (rc) return rc;
+    for (int32_t k = 0; k < n; ++k) sweeps_done[k] = b->slots[k].used ? (int64_t)d[k].sweep : -1;
+    return ISING_OK;
+}
+
 int ising_batch_observables(ising_batch_t b, int32_t idx, int64_t* M, int64_t* E, int64_t* sweeps_done)
 {
     int rc = check_batch(b, idx);

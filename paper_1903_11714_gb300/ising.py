@@ -55,6 +55,7 @@ _SIGS = {
     "ising_batch_remove": (ctypes.c_int, [_vp, _i32]),
     "ising_batch_run": (ctypes.c_int, [_vp, _i64, _i32]),
     "ising_batch_sweeps_done": (ctypes.c_int, [_vp, _i32, _P(_i64)]),
+    "ising_batch_progress": (ctypes.c_int, [_vp, _P(_i64), _i32]),
     "ising_batch_observables": (ctypes.c_int, [_vp, _i32, _P(_i64), _P(_i64), _P(_i64)]),
     "ising_batch_history": (ctypes.c_int, [_vp, _i32, _i64, _i64, _P(_i64), _P(_i64)]),
     "ising_batch_moments": (ctypes.c_int, [_vp, _i32, _i64, _P(_d), _P(_u64)]),
@@ -341,6 +342,11 @@ class Batch:
         n = ctypes.c_int64()
         _check(lib().ising_batch_sweeps_done(self.b, int(idx), ctypes.byref(n)))
         return n.value
+
+    def progress(self, n: int) -> np.ndarray:
+        out = np.zeros(max(n, 1), dtype=np.int64)
+        _check(lib().ising_batch_progress(self.b, _ptr(out, ctypes.c_int64), int(n)))
+        return out[:n]
 
     def observables(self, idx: int):
         M, E, n = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()

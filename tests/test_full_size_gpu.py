@@ -86,7 +86,7 @@ def test_int8_kernel_agrees_at_full_size(packed_run):
 def test_moments_at_full_magnetisation_of_the_largest_lattice():
     # cold start deep in the ordered phase: M = N = 2^32, so M^2 = 2^64 and M^4 = 2^128
     L = 65536
-    lat = ising.Lattice(L, 5.0, 3, ising.COLD, ising.PACKED).sweep(2)
+    lat = ising.Lattice(L, 200.0, 3, ising.COLD, ising.PACKED).sweep(2)  # T = 0: frozen
     M, E = lat.history()
     assert M.tolist() == [L * L, L * L] and E.tolist() == [-2 * L * L, -2 * L * L]
     got = lat.moments(0)
