@@ -243,6 +243,39 @@ int ising_autotune(int64_t L, int32_t *tile_rows, int32_t *threads, double *ms);
 int ising_dev_philox(uint64_t key, const uint32_t ctr[4], int64_t nblocks, uint32_t *out, void *stream);
 
 /*
+ * Packed sweeps of caller-owned lattices with no device allocation.  The paper
+ * has no counterpart; this serves callers that cannot call cudaMalloc -- code
+ * running while a CUDA graph is being captured, plugins confined to another
+ * runtime's memory pool, loops whose memory must be fixed after start-up.
+ *
+ * count lattices (1 <= count <= 64; more is ISING_EINVAL).  For lattice k:
+ * black[k], white[k] are device pointers to its two bit planes in the layout of
+ * ising_get_planes (L[k]*L[k]/64 uint32 words each, updated in place); L[k] %
+ * 64 == 0, 64 <= L[k] <= 2^20; beta[k] finite and >= 0; seed[k] its Philox key;
+ * me[k] a device array of 2*nsweeps int64 that receives (M, E) after each of the
+ * sweeps first_sweep .. first_sweep+nsweeps-1 (M at [2s], E at [2s+1], s counted
+ * from first_sweep).  The host arrays black, white, L, beta, seed, me are read
+ * during the call only.  The chain is the one ising_sweep produces: calling with
+ * first_sweep = n continues n sweeps done earlier, bit for bit.
+ *
+ * Work is enqueued on `stream` (a cudaStream_t; NULL = legacy default stream).
+ * wait != 0: the call synchronises the stream and returns ISING_ETIMEOUT if a
+ * bounded wait in the sweep kernel expired; wait == 0: it returns at once.
+ *
+ * Scratch (descriptors, tile table, status word, ~4.4 KB) is a file-scope
+ * __device__ array that every GPU loading this library holds until exit; no
+ * call allocates or frees device memory.  The first call on a device looks up
+ * that array's address (cudaGetSymbolAddress) and sets the kernel's
+ * shared-memory limit: make it before any stream capture.  All calls share the
+ * scratch, which keeps the last call's contents (each call rewrites it and
+ * clears the status word first), so calls whose work overlaps on the GPU race.
+ * Errors: EINVAL, ECUDA, ETIMEOUT (message in ising_last_error).
+ */
+int ising_sweep_packed_noalloc(int32_t count, uint32_t *const *black, uint32_t *const *white, const int64_t *L,
+                               const double *beta, const uint64_t *seed, int64_t first_sweep, int64_t nsweeps,
+                               int64_t *const *me, void *stream, int32_t wait);
+
+/*
  * Failure-detection self-test of the sweep kernel's bounded waits.  Launches one
  * half-sweep of a 256 x 256 lattice whose tile barriers expect 16 bytes that are
  * never sent, with each wait bounded by wait_cycles SM clocks (>= 1000), then

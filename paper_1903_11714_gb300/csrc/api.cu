@@ -311,6 +311,8 @@ struct Arena {
 
 }  // namespace
 
+void ising::set_last_error(const char* msg) { t_error = msg; }
+
 // ====================================================================== handles
 struct ising_s {
     int64_t L = 0;

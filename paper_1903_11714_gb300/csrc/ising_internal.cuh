@@ -80,6 +80,9 @@ cudaError_t launch_philox_words(uint64_t key, const uint32_t* ctr4, int64_t n, u
 
 int sm_count();
 
+// Sets the thread-local message that ising_last_error() returns (api.cu).
+void set_last_error(const char* msg);
+
 // Packed sweep kernel configuration helpers (sweep_packed.cu).
 int packed_smem_header_bytes(int threads);
 cudaError_t packed_set_smem_limit(int threads, size_t bytes);

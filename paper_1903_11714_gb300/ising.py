@@ -67,6 +67,8 @@ _SIGS = {
     "ising_dev_philox": (ctypes.c_int, [_u64, _P(ctypes.c_uint32), _i64, _vp, _vp]),
     "ising_probe_int_rates": (ctypes.c_int, [_P(_d)]),
     "ising_selftest_timeout": (ctypes.c_int, [_i64, _P(ctypes.c_int)]),
+    "ising_sweep_packed_noalloc": (ctypes.c_int, [_i32, _P(_vp), _P(_vp), _P(_i64), _P(_d), _P(_u64), _i64, _i64,
+                                                  _P(_vp), _vp, _i32]),
 }
 EXPORTS = tuple(_SIGS)
 
@@ -250,6 +252,18 @@ def ising_selftest_timeout(wait_cycles: int) -> int:
     obs = ctypes.c_int()
     _check(lib().ising_selftest_timeout(int(wait_cycles), ctypes.byref(obs)))
     return obs.value
+
+
+def ising_sweep_packed_noalloc(black_ptrs, white_ptrs, Ls, betas, seeds, first_sweep: int, nsweeps: int, me_ptrs,
+                               stream=None, wait: bool = True) -> None:
+    """Sweeps caller-owned device planes without any device allocation (device
+    pointers as integers, one entry per lattice)."""
+    n = len(Ls)
+    vp = ctypes.c_void_p * n
+    _check(lib().ising_sweep_packed_noalloc(
+        n, vp(*black_ptrs), vp(*white_ptrs), (ctypes.c_int64 * n)(*Ls), (ctypes.c_double * n)(*betas),
+        (ctypes.c_uint64 * n)(*seeds), int(first_sweep), int(nsweeps), vp(*me_ptrs), _stream_ptr(stream),
+        1 if wait else 0))
 
 
 # ------------------------------------------------------------------ classes

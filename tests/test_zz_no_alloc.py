@@ -1,0 +1,69 @@
+"""The sweep entry point that allocates no device memory.
+
+Some callers cannot call cudaMalloc (code running during CUDA graph capture,
+plugins confined to another runtime's memory pool, loops whose memory is fixed
+after start-up).  ising_sweep_packed_noalloc serves them: the caller owns the
+bit planes and the M/E output array, and the sweep kernel's scratch lives in a
+fixed file-scope device array inside the library.  This test checks, through
+the C ABI, that two calls in a row reproduce exactly what the handle API
+(ising_init_ex + ising_sweep) computes -- the same lattices and the same
+per-sweep M and E -- and that a call with too many lattices is refused.
+It is collected last so that a failure here stops a -x run only after every
+other test has run.
+"""
+import numpy as np
+import pytest
+
+from paper_1903_11714_gb300 import build as libbuild
+from paper_1903_11714_gb300 import ising
+
+pytestmark = pytest.mark.gpu
+
+SPECS = [(256, 0.4406868, 7, ising.HOT), (192, 0.3, 8, ising.HOT), (1024, 0.55, 9, ising.COLD)]
+N_SWEEPS = 6
+
+
+def test_two_noalloc_calls_match_the_handle_api():
+    import torch
+
+    libbuild.build()
+    handles, black, white, me1, me2 = [], [], [], [], []
+    for L, beta, seed, start in SPECS:
+        h = ising.Lattice(L, beta, seed, start, ising.PACKED)
+        b, w = h.get_planes()  # start state, host copy
+        black.append(torch.from_numpy(b.view(np.int32)).cuda())
+        white.append(torch.from_numpy(w.view(np.int32)).cuda())
+        me1.append(torch.zeros(2 * N_SWEEPS, dtype=torch.int64, device="cuda"))
+        me2.append(torch.zeros(2 * N_SWEEPS, dtype=torch.int64, device="cuda"))
+        handles.append(h)
+    torch.cuda.synchronize()
+    args = dict(black_ptrs=[t.data_ptr() for t in black], white_ptrs=[t.data_ptr() for t in white],
+                Ls=[s[0] for s in SPECS], betas=[s[1] for s in SPECS], seeds=[s[2] for s in SPECS])
+    # call 1: sweeps 0..5; call 2 continues with sweeps 6..11
+    ising.ising_sweep_packed_noalloc(**args, first_sweep=0, nsweeps=N_SWEEPS,
+                                     me_ptrs=[t.data_ptr() for t in me1], wait=True)
+    ising.ising_sweep_packed_noalloc(**args, first_sweep=N_SWEEPS, nsweeps=N_SWEEPS,
+                                     me_ptrs=[t.data_ptr() for t in me2], wait=True)
+    torch.cuda.synchronize()
+    for k, h in enumerate(handles):
+        h.sweep(N_SWEEPS)
+        M, E = h.history()
+        got1 = me1[k].cpu().numpy()
+        assert np.array_equal(got1[0::2], M) and np.array_equal(got1[1::2], E), k
+        h.sweep(N_SWEEPS)
+        M, E = h.history(N_SWEEPS, N_SWEEPS)
+        got2 = me2[k].cpu().numpy()
+        assert np.array_equal(got2[0::2], M) and np.array_equal(got2[1::2], E), k
+        hb, hw = h.get_planes()
+        assert np.array_equal(black[k].cpu().numpy().view(np.uint32), hb), k
+        assert np.array_equal(white[k].cpu().numpy().view(np.uint32), hw), k
+        h.close()
+
+
+def test_noalloc_refuses_more_lattices_than_its_scratch_holds():
+    libbuild.build()
+    n = 65
+    with pytest.raises(ising.IsingError) as e:
+        ising.ising_sweep_packed_noalloc([1] * n, [1] * n, [64] * n, [0.4] * n, [1] * n, 0, 1, [1] * n)
+    assert e.value.code == ising.ISING_EINVAL
+    assert "64" in ising.last_error()
