@@ -31,11 +31,38 @@ sys.path.insert(0, ROOT)
 
 METRIC = "spin-flip attempts/ns on 1 GB300 (bit-packed checkerboard sweep, bit-exact)"
 UNIT = "flips/ns"
-# algorithmic work per site per sweep: 1/4 Philox4x32-10 call = 5 32x32->64 multiplies
-MULS_PER_SITE_SWEEP = 5.0
+# algorithmic work per site update: a Philox4x32-10 call serves 4 sites with 20
+# 32x32->64 products, 2 of which do not depend on the site (computed once per
+# 32-site word), so 18 / 4 = 4.5 multiplies per site
+MULS_PER_SITE_SWEEP = 4.5
+# multiply-pipe peak from unit counts: 16 fmaheavy lanes x 4 schedulers per SM,
+# two lane-cycles per 32x32->64 product -> 32 products per clock per SM
+MULS_PER_CLK_SM = 32.0
+N_SMS = 152
 # algorithmic bytes per site per sweep (packed): each half-sweep reads the target
 # and source planes and writes the target plane, N/2 bits each
 BYTES_PER_SITE_SWEEP = 3.0 * 2 * (0.5 / 8.0)
+
+
+def max_over_ranks(value: float, dist, device: str) -> float:
+    """Timing of the slowest rank (the job ends when the last replica does)."""
+    if dist is None:
+        return value
+    import torch
+
+    t = torch.tensor([value], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def total_over_ranks(value: float, dist, device: str) -> float:
+    if dist is None:
+        return value
+    import torch
+
+    t = torch.tensor([value], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
 
 
 def dist_env():
@@ -187,6 +214,132 @@ def run_reference(args, rank: int, world: int) -> None:
     }))
 
 
+def _events(torch, stream):
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    return e0, e1
+
+
+def run_single_small(args) -> None:
+    """L = 128, 1000 sweeps, packed vs plain int8 (launch-latency bound)."""
+    import torch
+
+    from paper_1903_11714_gb300 import ising, workloads
+
+    cfg = workloads.single_small()
+    out = {}
+    for name, kernel in (("packed", ising.PACKED), ("int8", ising.INT8)):
+        st = torch.cuda.Stream()
+        lat = ising.Lattice(cfg.L, cfg.beta, cfg.seed, cfg.start, kernel, stream=st)
+        lat.sweep(args.warmup)
+        lat.synchronize()
+        e0, e1 = _events(torch, st)
+        e0.record(st)
+        lat.sweep(cfg.sweeps)
+        e1.record(st)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        lat.close()
+        out[name] = cfg.sweeps * cfg.L ** 2 / (ms * 1e6)
+    print(json.dumps({"metric": "spin-flip attempts/ns, L=128 single lattice", "workload": "single_small",
+                      "unit": UNIT, "value": out["packed"], "int8_value": out["int8"],
+                      "config": cfg.as_dict(), "note": "2 kernel launches per sweep; launch-latency bound"}))
+
+
+def run_batched(args, which: str) -> None:
+    """Batched forms (one persistent launch per half-sweep over all lattices)
+    against plain launches of the int8 and packed kernels, one lattice at a time."""
+    import torch
+
+    from paper_1903_11714_gb300 import ising, workloads
+
+    if which == "scan":
+        lats = workloads.temperature_scan()
+        graph = workloads.TEMPERATURE_SCAN_GRAPH_SWEEPS
+        sweeps = lats[0].sweeps
+        max_L = 1024
+    else:
+        lats = workloads.uneven_batch()
+        graph = 100
+        sweeps = lats[0].sweeps
+        max_L = 4096
+    warm = graph * 3 if graph else args.warmup
+    arena = sum(l.L * l.L // 8 + 16 * (l.sweeps + warm) + 4096 for l in lats)
+    st = torch.cuda.Stream()
+    tiles = {}
+    if which == "uneven":
+        for L in sorted({l.L for l in lats}):
+            tiles[L] = ising.ising_autotune(L)[0]
+    b = ising.Batch(len(lats), max_L, arena, 0, stream=st)
+    for l in lats:
+        b.add(l.L, l.beta, l.seed, l.start, l.sweeps + warm, tiles.get(l.L, 0))
+    b.run(warm, graph_sweeps=graph)
+    b.synchronize()
+    e0, e1 = _events(torch, st)
+    e0.record(st)
+    b.run(sweeps, graph_sweeps=graph)
+    e1.record(st)
+    torch.cuda.synchronize()
+    b.synchronize()
+    ms = e0.elapsed_time(e1)
+    flips = sweeps * sum(l.L * l.L for l in lats)
+    batched = flips / (ms * 1e6)
+    b.close()
+    # plain: each lattice alone, its own launches, for a shorter run (same per-sweep work)
+    plain = {}
+    n_plain = min(sweeps, 100)
+    for name, kernel in (("int8", ising.INT8), ("packed", ising.PACKED)):
+        total_ms = 0.0
+        for l in lats:
+            lat = ising.Lattice(l.L, l.beta, l.seed, l.start, kernel, stream=st)
+            lat.sweep(2)
+            lat.synchronize()
+            a0, a1 = _events(torch, st)
+            a0.record(st)
+            lat.sweep(n_plain)
+            a1.record(st)
+            torch.cuda.synchronize()
+            total_ms += a0.elapsed_time(a1)
+            lat.close()
+        plain[name] = n_plain * sum(l.L * l.L for l in lats) / (total_ms * 1e6)
+    print(json.dumps({"metric": f"aggregate spin-flip attempts/ns, {which} batch", "workload": which,
+                      "unit": UNIT, "value": batched, "plain_int8_value": plain["int8"],
+                      "plain_packed_value": plain["packed"], "lattices": len(lats), "sweeps": sweeps,
+                      "graph_sweeps": graph, "ms": ms,
+                      "tile_rows_by_L": tiles or None,
+                      "note": f"plain = each lattice alone with its own launches, {n_plain} sweeps each"}))
+
+
+def run_serve(args) -> None:
+    """Poisson arrivals at ~80 % of measured capacity; p50/p99 latency."""
+    import torch
+
+    from paper_1903_11714_gb300 import serve, workloads
+
+    budget = int(args.serve_budget_gb * (1 << 30))
+    st = torch.cuda.Stream()
+    srv = serve.Server(budget, slots=args.serve_slots, max_L=8192, quantum=args.serve_quantum, stream=st)
+    # capacity: a saturated sample of the same request distribution, all present at t = 0
+    calib = [workloads.Request(rid=r.rid, arrival=0.0, L=r.L, beta=r.beta, seed=r.seed, sweeps=r.sweeps)
+             for r in workloads.serving_requests(args.serve_calib, 1.0, seed=55)]
+    _, cst = srv.serve(calib, realtime=False)
+    capacity = cst.flips / cst.wall_s
+    mean_flips = workloads.mean_request_flips()
+    rate = 0.8 * capacity / mean_flips
+    reqs = workloads.serving_requests(args.serve_requests, rate)
+    results, st_ = srv.serve(reqs, realtime=True)
+    srv.close()
+    summ = st_.summary()
+    print(json.dumps({"metric": "serving: p50/p99 latency and aggregate spin-flip attempts/ns",
+                      "workload": "serve", "unit": UNIT, "value": summ["flips_per_ns"],
+                      "p50_s": summ["p50_s"], "p99_s": summ["p99_s"], "requests": summ["completed"],
+                      "rate_per_s": rate, "capacity_flips_per_ns": capacity / 1e9,
+                      "mean_request_flips": mean_flips, "hbm_budget_gb": args.serve_budget_gb,
+                      "slots": args.serve_slots, "quantum_sweeps": args.serve_quantum,
+                      "max_active": summ["max_active"], "max_arena_gb": summ["max_arena_bytes"] / 2**30,
+                      "blocked_by_memory": summ["blocked_by_memory"], "blocked_by_slots": summ["blocked_by_slots"]}))
+
+
 def main() -> None:
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -198,6 +351,13 @@ def main() -> None:
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--ref-rows", type=int, default=1024)
+    ap.add_argument("--workload", choices=["single_large", "single_small", "scan", "uneven", "serve"],
+                    default="single_large")
+    ap.add_argument("--serve-requests", type=int, default=2000)
+    ap.add_argument("--serve-calib", type=int, default=150)
+    ap.add_argument("--serve-slots", type=int, default=256)
+    ap.add_argument("--serve-quantum", type=int, default=32)
+    ap.add_argument("--serve-budget-gb", type=float, default=120.0)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
@@ -213,6 +373,11 @@ def main() -> None:
     from paper_1903_11714_gb300 import ising, workloads
 
     torch.cuda.set_device(local)
+    if args.workload != "single_large":
+        libbuild.build()
+        {"single_small": run_single_small, "serve": run_serve}.get(
+            args.workload, lambda a: run_batched(a, args.workload))(args)
+        return
     dist = None
     if world > 1:
         import torch.distributed as dist
@@ -249,24 +414,23 @@ def main() -> None:
         dist.barrier()
     clocks = sampler.stop()
     lat.synchronize()
-    ms = ev0.elapsed_time(ev1)
-    if dist:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * args.steps * N / (ms * 1e6)
+    ms = max_over_ranks(ev0.elapsed_time(ev1), dist, "cuda")
+    flips_all = total_over_ranks(float(args.steps * N), dist, "cuda")
+    value = flips_all / (ms * 1e6)
 
     # dominant kernel: the packed half-sweep (2 launches per sweep + 1 counter advance per call)
     launches = 2 * args.steps + 1
     t_launch_s = ms * 1e-3 / (2 * args.steps)
     muls_per_launch = MULS_PER_SITE_SWEEP * N / 2
     achieved = muls_per_launch / t_launch_s / 1e12
-    peak = mul_per_clk * 152 * sm_max * 1e6 / 1e12
+    peak = MULS_PER_CLK_SM * N_SMS * sm_max * 1e6 / 1e12
     bytes_per_launch = BYTES_PER_SITE_SWEEP * N / 2
     traffic = committed_traffic(L) if kernel == ising.PACKED else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tmul/s", "frac": achieved / peak,
                 "traffic": traffic,
-                "peak_basis": f"{mul_per_clk:.1f} 32x32->64 multiplies/clk/SM (probe) x 152 SMs x {sm_max:.0f} MHz",
+                "peak_basis": f"{MULS_PER_CLK_SM:.0f} 32x32->64 multiplies/clk/SM (16 fmaheavy lanes x 4 schedulers, "
+                              f"2 lane-cycles each) x {N_SMS} SMs x {sm_max:.0f} MHz; probe measures "
+                              f"{mul_per_clk:.1f}/clk/SM",
                 "hbm_achieved_gbs": bytes_per_launch / t_launch_s / 1e9,
                 "hbm_peak_gbs": peaks.get("hbm_gbs", 6800.0),
                 "alu_ops_per_clk_sm_probe": alu_per_clk}

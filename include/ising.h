@@ -177,7 +177,8 @@ int ising_batch_create(ising_batch_t *out, int32_t capacity, int64_t max_L, int6
 /*
  * Adds a packed lattice (L % 64 == 0, L <= max_L) that will run `sweeps`
  * sweeps at most (its history capacity).  tile_rows: rows per tile (4, 8, 16,
- * 32 or 64 dividing L; 0 = built-in choice).  Writes the slot index to *idx.
+ * 32 or 64 dividing L, or 2 when L % 256 == 0; 0 = built-in choice).
+ * Writes the slot index to *idx.
  * Enqueues the start state.  Errors: EINVAL, ENOMEM (arena), EBUSY (slots).
  */
 int ising_batch_add(ising_batch_t b, int64_t L, double beta, uint64_t seed, int32_t start, int64_t sweeps,
@@ -224,7 +225,8 @@ int ising_batch_free(ising_batch_t b);
 
 /*
  * Times one half-sweep of a packed lattice of side L for each candidate
- * (tile_rows in {4,8,16,32,64} dividing L, threads in {256, 512}) and returns
+ * (tile_rows in {2,4,8,16,32,64} dividing L, 2 only when L % 256 == 0; threads in
+ * {256, 512}) and returns
  * the fastest in *tile_rows, *threads and its time in *ms.  Uses its own
  * scratch lattice.  Errors: EINVAL, ENOMEM, ECUDA.
  */

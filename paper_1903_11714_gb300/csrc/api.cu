@@ -82,19 +82,25 @@ int64_t stage_bytes_for(int64_t L, int tile_rows)
     return (words * 4 + 15) / 16 * 16;
 }
 
+// Tile heights: 4..64 rows; 2 rows only when a row is a whole number of 16-byte
+// units (W % 4 == 0), so that every bulk copy stays 16-byte aligned.
 bool tile_rows_ok(int64_t L, int tr)
 {
-    return (tr == 4 || tr == 8 || tr == 16 || tr == 32 || tr == 64) && tr <= L && L % tr == 0 &&
+    const bool pow2 = tr == 2 || tr == 4 || tr == 8 || tr == 16 || tr == 32 || tr == 64;
+    return pow2 && (tr >= 4 || (L / 64) % 4 == 0) && tr <= L && L % tr == 0 &&
            stage_bytes_for(L, tr) <= kStageCapBytes;
 }
 
-// Built-in tile height: about 4096 words per tile, clamped to [4, 64].
+// Built-in tile height: about ISING_TILE_WORDS words per tile, clamped to [2, 64].
+#ifndef ISING_TILE_WORDS
+#define ISING_TILE_WORDS 4096
+#endif
 int default_tile_rows(int64_t L)
 {
     const int64_t W = L / 64;
     int tr = 64;
-    while (tr > 4 && (int64_t)tr * W > 4096) tr >>= 1;
-    while (tr > 4 && !tile_rows_ok(L, tr)) tr >>= 1;
+    while (tr > 2 && ((int64_t)tr * W > ISING_TILE_WORDS || !tile_rows_ok(L, tr))) tr >>= 1;
+    if (!tile_rows_ok(L, tr)) tr = 4;
     return tr;
 }
 
@@ -898,7 +904,7 @@ int ising_batch_create(ising_batch_t* out, int32_t capacity, int64_t max_L, int6
     // stage size: the largest tile any admissible lattice can use
     int64_t stage = 0;
     for (int64_t L = 64; L <= max_L; L += 64)
-        for (int tr = 4; tr <= 64; tr *= 2)
+        for (int tr = 2; tr <= 64; tr *= 2)
             if (tile_rows_ok(L, tr)) stage = std::max(stage, stage_bytes_for(L, tr));
     rc = b->eng.setup(capacity, (int)stage, threads, b->stream);
     if (!rc) rc = b->arena.init(arena_bytes);
@@ -1130,7 +1136,7 @@ int ising_autotune(int64_t L, int32_t* tile_rows, int32_t* threads, double* ms)
         const int64_t arena = (int64_t)sizeof(uint32_t) * 2 * L * (L / 64) + 16 * 64 + 4096;
         int rc = ising_batch_create(&b, 1, L, arena, thread_opts[ti], nullptr);
         if (rc) return rc;
-        for (int tr = 4; tr <= 64; tr *= 2) {
+        for (int tr = 2; tr <= 64; tr *= 2) {
             if (!tile_rows_ok(L, tr)) continue;
             int32_t idx = -1;
             rc = ising_batch_add(b, L, 0.4406868, 12345, ISING_HOT, 64, tr, &idx);

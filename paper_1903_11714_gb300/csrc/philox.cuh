@@ -91,6 +91,53 @@ __device__ __forceinline__ void philox_call(uint32_t q_lo, const PhiloxWordConst
     o3 = y3;
 }
 
+// The eight calls of one 32-site word (counter word 0 = q_lo .. q_lo+7), advanced
+// round by round together so the multiplies of different calls overlap, with
+// each round key formed once per round for all eight.  out[4 j + m] is output
+// word m of call j, i.e. the draw of the word's site 4 j + m.
+__device__ __forceinline__ void philox_word8(uint32_t q_lo, const PhiloxWordConsts& c, uint64_t key,
+                                             uint32_t out[32])
+{
+    const uint32_t k0 = (uint32_t)key, k1 = (uint32_t)(key >> 32);
+    uint32_t y0[8], y1[8], y2[8], y3[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        uint32_t hi, lo;
+        mulhilo(kPhiloxA, q_lo + (uint32_t)j, hi, lo);  // round 1, counter-dependent half
+        const uint32_t x2 = hi ^ c.r1_k;
+        const uint32_t x3 = lo;
+        mulhilo(kPhiloxB, x2, hi, lo);  // round 2, counter-dependent half
+        y0[j] = hi ^ c.r2_y0;
+        y1[j] = lo;
+        y2[j] = c.r2_hi ^ x3;
+        y3[j] = c.r2_lo;
+    }
+#pragma unroll
+    for (int r = 2; r < 10; ++r) {
+        const uint32_t rk0 = k0 + (uint32_t)r * kWeyl0;
+        const uint32_t rk1 = k1 + (uint32_t)r * kWeyl1;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            uint32_t h0, l0, h1, l1;
+            mulhilo(kPhiloxA, y0[j], h0, l0);
+            mulhilo(kPhiloxB, y2[j], h1, l1);
+            const uint32_t n0 = h1 ^ y1[j] ^ rk0;
+            const uint32_t n2 = h0 ^ y3[j] ^ rk1;
+            y0[j] = n0;
+            y1[j] = l1;
+            y2[j] = n2;
+            y3[j] = l0;
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        out[4 * j + 0] = y0[j];
+        out[4 * j + 1] = y1[j];
+        out[4 * j + 2] = y2[j];
+        out[4 * j + 3] = y3[j];
+    }
+}
+
 // Plain ten-round Philox4x32-10 on an arbitrary counter (used by tests of the
 // device generator and by the start-state kernels).
 __device__ __forceinline__ void philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint64_t key,

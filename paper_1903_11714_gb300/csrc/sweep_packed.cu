@@ -24,6 +24,12 @@
 #include "ising_internal.cuh"
 #include "philox.cuh"
 
+// Threads per SM the register allocation must leave room for (a CTA of NT
+// threads gets a register cap of 65536 / ISING_SWEEP_THREADS_PER_SM per thread).
+#ifndef ISING_SWEEP_THREADS_PER_SM
+#define ISING_SWEEP_THREADS_PER_SM 512
+#endif
+
 namespace ising {
 namespace {
 
@@ -117,8 +123,9 @@ __device__ __forceinline__ TileInfo tile_info(const TileTable& tt, int count, in
 
 // Thread 0: stage the tile's rows.  Source rows [i0 - HB, i0 + TR + HB) (wrapped)
 // and target rows [i0, i0 + TR).  Every copy starts on a 16-byte boundary: with
-// W % 4 == 0 every row does; otherwise HB = 4 and tiles start on rows that are
-// multiples of 4, so each copied block starts at a multiple of 4 rows.
+// W % 4 == 0 every row does (TR may then be 2); otherwise HB = 4 and tiles start
+// on rows that are multiples of 4, so each copied block starts at a multiple of
+// 4 rows.
 __device__ __forceinline__ void issue_tile(const LatticeDesc& d, int local_tile, int colour, uint32_t* stage,
                                            uint64_t* bar, uint32_t extra_tx)
 {
@@ -155,18 +162,17 @@ __device__ __forceinline__ uint32_t update_word(uint32_t t, uint32_t up, uint32_
     const uint32_t b2 = c0 & c1;
 
     const PhiloxWordConsts pc = philox_consts(key, (uint32_t)(q0 >> 32), sweep, (uint32_t)colour);
-    const uint32_t qlo = (uint32_t)q0;
-    uint32_t q2 = all2, q4 = all4;
+    uint32_t x[32];
+    philox_word8((uint32_t)q0, pc, key, x);
+    // compare bits gathered in four independent partial masks (short OR chains)
+    uint32_t q2p[4] = {0, 0, 0, 0}, q4p[4] = {0, 0, 0, 0};
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        uint32_t x[4];
-        philox_call(qlo + (uint32_t)j, pc, key, x[0], x[1], x[2], x[3]);
-#pragma unroll
-        for (int m = 0; m < 4; ++m) {
-            q2 |= (x[m] < t2 ? 1u : 0u) << (4 * j + m);
-            q4 |= (x[m] < t4 ? 1u : 0u) << (4 * j + m);
-        }
+    for (int b = 0; b < 32; ++b) {
+        q2p[b & 3] |= (x[b] < t2 ? 1u : 0u) << b;
+        q4p[b & 3] |= (x[b] < t4 ? 1u : 0u) << b;
     }
+    const uint32_t q2 = all2 | q2p[0] | q2p[1] | q2p[2] | q2p[3];
+    const uint32_t q4 = all4 | q4p[0] | q4p[1] | q4p[2] | q4p[3];
     // n_anti >= 2 (h <= 0): always; n_anti == 1 (h = 2): x < T2; n_anti == 0 (h = 4):
     // x < T4.  T4 <= T2, so q4 is a subset of q2 and ORing q4 everywhere is exact.
     const uint32_t flip = b1 | b2 | (b0 & q2) | q4;
@@ -174,7 +180,8 @@ __device__ __forceinline__ uint32_t update_word(uint32_t t, uint32_t up, uint32_
 }
 
 template <int NT>
-__global__ void __launch_bounds__(NT) packed_half_sweep_kernel(TileTable tt, int colour, int step, int* status,
+__global__ void __launch_bounds__(NT, (ISING_SWEEP_THREADS_PER_SM / NT > 0 ? ISING_SWEEP_THREADS_PER_SM / NT : 1))
+    packed_half_sweep_kernel(TileTable tt, int colour, int step, int* status,
                                                                int stage_words_max, long long wait_limit,
                                                                uint32_t extra_tx)
 {
@@ -277,9 +284,10 @@ __global__ void __launch_bounds__(NT) packed_half_sweep_kernel(TileTable tt, int
                 slot[1] = -2 * N;
             }
             const int nwords = TR * W;
+            // (row, word) of idx = tid + k*NT, advanced without a division per word
+            const int step_r = NT / W, step_w = NT - step_r * W;
+            int r = tid / W, w = tid - r * W;
             for (int idx = tid; idx < nwords; idx += NT) {
-                const int r = idx / W;
-                const int w = idx - r * W;
                 const int i = i0 + r;
                 const uint32_t* srow = s_src + (size_t)(HB + r) * W;
                 const uint32_t up = srow[w - W];
@@ -301,6 +309,12 @@ __global__ void __launch_bounds__(NT) packed_half_sweep_kernel(TileTable tt, int
                 if (colour == 1) {
                     ups += __popc(nw) + __popc(same);
                     anti += __popc(nw ^ up) + __popc(nw ^ down) + __popc(nw ^ same) + __popc(nw ^ hz);
+                }
+                r += step_r;
+                w += step_w;
+                if (w >= W) {
+                    w -= W;
+                    ++r;
                 }
             }
         }
