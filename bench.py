@@ -424,7 +424,8 @@ def main() -> None:
     muls_per_launch = MULS_PER_SITE_SWEEP * N / 2
     achieved = muls_per_launch / t_launch_s / 1e12
     peak = MULS_PER_CLK_SM * N_SMS * sm_max * 1e6 / 1e12
-    bytes_per_launch = BYTES_PER_SITE_SWEEP * N / 2
+    # packed: 3 planes of N/2 bits per half-sweep; int8: the whole lattice read and written
+    bytes_per_launch = BYTES_PER_SITE_SWEEP * N / 2 if kernel == ising.PACKED else 2.0 * N
     traffic = committed_traffic(L) if kernel == ising.PACKED else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tmul/s", "frac": achieved / peak,
                 "traffic": traffic,

@@ -119,6 +119,10 @@ struct Engine {
     int* d_status = nullptr;
     cudaGraphExec_t gexec = nullptr;
     int g_sweeps = 0;
+    // single-lattice handles: host copy of the descriptor, whose sweep field the
+    // handle keeps equal to the device's; plain launches then pass it by value
+    const LatticeDesc* one = nullptr;
+    bool capturing = false;
 
     int setup(int max_count_, int stage_bytes_, int threads_, cudaStream_t s)
     {
@@ -184,9 +188,11 @@ struct Engine {
     int enqueue_sweeps(int64_t n)
     {
         const TileTable tt = table();
+        const LatticeDesc* by_value = capturing ? nullptr : one;
         for (int64_t k = 0; k < n; ++k) {
             for (int c = 0; c < 2; ++c) {
-                cudaError_t e = launch_packed_half_sweep(tt, c, (int)k, d_status, grid, threads, stage_bytes, stream);
+                cudaError_t e = launch_packed_half_sweep(tt, c, (int)k, d_status, grid, threads, stage_bytes, stream,
+                                                         kWaitLimitCycles, 0u, by_value);
                 if (e != cudaSuccess) return cuda_fail(e, "packed half-sweep launch");
             }
         }
@@ -204,7 +210,9 @@ struct Engine {
         if (!gexec || g_sweeps != graph_sweeps) {
             drop_graph();
             CK(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
+            capturing = true;
             int rc = enqueue_sweeps(graph_sweeps);
+            capturing = false;
             cudaGraph_t g = nullptr;
             cudaError_t e = cudaStreamEndCapture(stream, &g);
             if (rc != ISING_OK) {
@@ -555,6 +563,7 @@ int ising_init_ex(ising_t* out, int64_t L, double beta, uint64_t seed, int start
             destroy_handle(h);
             return rc;
         }
+        h->eng.one = &h->desc;
         std::vector<int32_t> ts = {0, (int32_t)(L / tr)};
         rc = h->eng.upload_tiles(ts, 1);
         if (!rc) rc = ensure_hist(h, 1024);

@@ -50,9 +50,13 @@ constexpr long long kWaitLimitCycles = 4000000000LL;
 
 // Launchers (return cudaError_t of the launch).  extra_tx > 0 makes every tile
 // barrier expect bytes that never arrive: only the timeout self-test uses it.
+// one != nullptr: a launch over that single lattice, whose descriptor (with the
+// sweep index the host knows) is passed by value; tt is then not read.  Not for
+// graph capture, since the sweep index is baked into the launch.
 cudaError_t launch_packed_half_sweep(const TileTable& tt, int colour, int step, int* status, int grid,
                                      int threads, int smem_stage_bytes, cudaStream_t s,
-                                     long long wait_limit = kWaitLimitCycles, uint32_t extra_tx = 0);
+                                     long long wait_limit = kWaitLimitCycles, uint32_t extra_tx = 0,
+                                     const LatticeDesc* one = nullptr);
 cudaError_t launch_packed_advance(LatticeDesc* desc, const int32_t* count, int max_count, int steps,
                                   cudaStream_t s);
 cudaError_t launch_packed_init(uint32_t* black, uint32_t* white, int64_t L, uint64_t key, int start,

@@ -112,13 +112,36 @@ struct TileInfo {
     bool live;
 };
 
-__device__ __forceinline__ TileInfo tile_info(const TileTable& tt, int count, int t, int step)
+// Descriptor of lattice `lat`: from the device table, or -- for a launch over a
+// single lattice (ONE) -- from the kernel parameter, whose fields are then
+// launch-uniform operands (round keys, thresholds) instead of per-thread loads.
+template <bool ONE>
+__device__ __forceinline__ const LatticeDesc& desc_at(const TileTable& tt, const LatticeDesc& one, int lat)
+{
+    if constexpr (ONE)
+        return one;
+    else
+        return tt.desc[lat];
+}
+
+template <bool ONE>
+__device__ __forceinline__ TileInfo tile_info(const TileTable& tt, const LatticeDesc& one, int count, int t,
+                                              int step)
 {
     TileInfo ti;
-    ti.lat = lattice_of_tile(tt.tile_start, count, t);
-    const LatticeDesc& d = tt.desc[ti.lat];
+    ti.lat = ONE ? 0 : lattice_of_tile(tt.tile_start, count, t);
+    const LatticeDesc& d = desc_at<ONE>(tt, one, ti.lat);
     ti.live = d.active && (d.sweep + (uint32_t)step < d.target);
     return ti;
+}
+
+template <bool ONE>
+__device__ __forceinline__ int tile_base(const TileTable& tt, int lat)
+{
+    if constexpr (ONE)
+        return 0;
+    else
+        return __ldg(tt.tile_start + lat);
 }
 
 // Thread 0: stage the tile's rows.  Source rows [i0 - HB, i0 + TR + HB) (wrapped)
@@ -149,8 +172,8 @@ __device__ __forceinline__ void issue_tile(const LatticeDesc& d, int local_tile,
 
 // New value of one 32-site target word.
 __device__ __forceinline__ uint32_t update_word(uint32_t t, uint32_t up, uint32_t down, uint32_t same,
-                                                uint32_t hz, uint64_t q0, uint64_t key, uint32_t sweep,
-                                                int colour, uint32_t t2, uint32_t t4, uint32_t all2,
+                                                uint32_t hz, uint32_t q_lo, const PhiloxWordConsts& pc,
+                                                uint64_t key, uint32_t t2, uint32_t t4, uint32_t all2,
                                                 uint32_t all4)
 {
     // anti-aligned neighbour bits and their 4-input sum n_anti = 4*b2 + 2*b1 + b0
@@ -161,9 +184,8 @@ __device__ __forceinline__ uint32_t update_word(uint32_t t, uint32_t up, uint32_
     const uint32_t b1 = c0 ^ c1 ^ cc;
     const uint32_t b2 = c0 & c1;
 
-    const PhiloxWordConsts pc = philox_consts(key, (uint32_t)(q0 >> 32), sweep, (uint32_t)colour);
     uint32_t x[32];
-    philox_word8((uint32_t)q0, pc, key, x);
+    philox_word8(q_lo, pc, key, x);
     // compare bits gathered in four independent partial masks (short OR chains)
     uint32_t q2p[4] = {0, 0, 0, 0}, q4p[4] = {0, 0, 0, 0};
 #pragma unroll
@@ -179,19 +201,18 @@ __device__ __forceinline__ uint32_t update_word(uint32_t t, uint32_t up, uint32_
     return t ^ flip;
 }
 
-template <int NT>
+template <int NT, bool ONE>
 __global__ void __launch_bounds__(NT, (ISING_SWEEP_THREADS_PER_SM / NT > 0 ? ISING_SWEEP_THREADS_PER_SM / NT : 1))
-    packed_half_sweep_kernel(TileTable tt, int colour, int step, int* status,
-                                                               int stage_words_max, long long wait_limit,
-                                                               uint32_t extra_tx)
+    packed_half_sweep_kernel(TileTable tt, const __grid_constant__ LatticeDesc one, int colour, int step,
+                             int* status, int stage_words_max, long long wait_limit, uint32_t extra_tx)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);
     uint32_t* red = reinterpret_cast<uint32_t*>(smem_raw + 16);  // 2 * NT/32 words
     uint32_t* stages = reinterpret_cast<uint32_t*>(smem_raw + 128 + ((2 * (NT / 32) * 4 + 127) / 128) * 128);
     const int tid = threadIdx.x;
-    const int count = *tt.count;
-    const int total = __ldg(tt.tile_start + count);
+    const int count = ONE ? 1 : *tt.count;
+    const int total = ONE ? one.L / one.tile_rows : __ldg(tt.tile_start + count);
 
     if (tid == 0) {
         mbar_init(&bars[0], 1);
@@ -205,9 +226,10 @@ __global__ void __launch_bounds__(NT, (ISING_SWEEP_THREADS_PER_SM / NT > 0 ? ISI
     int t = blockIdx.x;
     TileInfo cur = {0, false};
     if (t < total) {
-        cur = tile_info(tt, count, t, step);
+        cur = tile_info<ONE>(tt, one, count, t, step);
         if (cur.live && tid == 0)
-            issue_tile(tt.desc[cur.lat], t - __ldg(tt.tile_start + cur.lat), colour, stages, &bars[0], extra_tx);
+            issue_tile(desc_at<ONE>(tt, one, cur.lat), t - tile_base<ONE>(tt, cur.lat), colour, stages, &bars[0],
+                       extra_tx);
     }
 
     int acc_lat = -1;          // lattice whose M/E counts are being accumulated
@@ -228,7 +250,7 @@ __global__ void __launch_bounds__(NT, (ISING_SWEEP_THREADS_PER_SM / NT > 0 ? ISI
                 su += red[2 * k];
                 sa += red[2 * k + 1];
             }
-            const LatticeDesc& d = tt.desc[lat];
+            const LatticeDesc& d = desc_at<ONE>(tt, one, lat);
             int64_t* slot = d.hist + 2 * (int64_t)(d.sweep + (uint32_t)step);
             atomicAdd(reinterpret_cast<unsigned long long*>(slot), 2ull * su);
             atomicAdd(reinterpret_cast<unsigned long long*>(slot + 1), 2ull * sa);
@@ -242,16 +264,16 @@ __global__ void __launch_bounds__(NT, (ISING_SWEEP_THREADS_PER_SM / NT > 0 ? ISI
         const int tn = t + gridDim.x;
         TileInfo nxt = {0, false};
         if (tn < total) {
-            nxt = tile_info(tt, count, tn, step);
+            nxt = tile_info<ONE>(tt, one, count, tn, step);
             if (nxt.live && tid == 0) {
                 fence_proxy_async_smem();
-                issue_tile(tt.desc[nxt.lat], tn - __ldg(tt.tile_start + nxt.lat), colour,
+                issue_tile(desc_at<ONE>(tt, one, nxt.lat), tn - tile_base<ONE>(tt, nxt.lat), colour,
                            stages + (size_t)(buf ^ 1) * stage_words_max, &bars[buf ^ 1], extra_tx);
             }
         }
         if (cur.live) {
-            const LatticeDesc& d = tt.desc[cur.lat];
-            const int local_tile = t - __ldg(tt.tile_start + cur.lat);
+            const LatticeDesc& d = desc_at<ONE>(tt, one, cur.lat);
+            const int local_tile = t - tile_base<ONE>(tt, cur.lat);
             const uint32_t parity = buf ? phase1 : phase0;
             bool ok = mbar_wait_bounded(&bars[buf], parity, wait_limit);
             if (buf)
@@ -283,6 +305,10 @@ __global__ void __launch_bounds__(NT, (ISING_SWEEP_THREADS_PER_SM / NT > 0 ? ISI
                 slot[0] = -N;
                 slot[1] = -2 * N;
             }
+            // counter words q = i*L/8 + 8w stay below 2^32 when L <= 131072, so the
+            // per-word Philox constants (which depend on q's high word) are fixed
+            const bool q_small = L <= 131072;
+            const PhiloxWordConsts pc_tile = philox_consts(key, 0u, sweep, (uint32_t)colour);
             const int nwords = TR * W;
             // (row, word) of idx = tid + k*NT, advanced without a division per word
             const int step_r = NT / W, step_w = NT - step_r * W;
@@ -304,7 +330,9 @@ __global__ void __launch_bounds__(NT, (ISING_SWEEP_THREADS_PER_SM / NT > 0 ? ISI
                 }
                 const uint32_t tw = s_tgt[idx];
                 const uint64_t q0 = (uint64_t)i * (uint64_t)(L >> 3) + 8ull * (uint64_t)w;
-                const uint32_t nw = update_word(tw, up, down, same, hz, q0, key, sweep, colour, t2, t4, all2, all4);
+                const PhiloxWordConsts pc =
+                    q_small ? pc_tile : philox_consts(key, (uint32_t)(q0 >> 32), sweep, (uint32_t)colour);
+                const uint32_t nw = update_word(tw, up, down, same, hz, (uint32_t)q0, pc, key, t2, t4, all2, all4);
                 out_plane[(size_t)i * W + w] = nw;
                 if (colour == 1) {
                     ups += __popc(nw) + __popc(same);
@@ -344,20 +372,33 @@ int packed_smem_header_bytes(int threads)
     return 128 + ((2 * (threads / 32) * 4 + 127) / 128) * 128;
 }
 
+template <int NT>
+void launch_nt(const TileTable& tt, const LatticeDesc* one, int colour, int step, int* status, int grid, size_t smem,
+               int stage_words, cudaStream_t s, long long wait_limit, uint32_t extra_tx)
+{
+    if (one)
+        packed_half_sweep_kernel<NT, true><<<grid, NT, smem, s>>>(tt, *one, colour, step, status, stage_words,
+                                                                  wait_limit, extra_tx);
+    else
+        packed_half_sweep_kernel<NT, false><<<grid, NT, smem, s>>>(tt, LatticeDesc{}, colour, step, status,
+                                                                   stage_words, wait_limit, extra_tx);
+}
+
 cudaError_t launch_packed_half_sweep(const TileTable& tt, int colour, int step, int* status, int grid, int threads,
-                                     int smem_stage_bytes, cudaStream_t s, long long wait_limit, uint32_t extra_tx)
+                                     int smem_stage_bytes, cudaStream_t s, long long wait_limit, uint32_t extra_tx,
+                                     const LatticeDesc* one)
 {
     const int stage_words = smem_stage_bytes / 4;
     const size_t smem = (size_t)packed_smem_header_bytes(threads) + 2 * (size_t)smem_stage_bytes;
     switch (threads) {
     case 128:
-        packed_half_sweep_kernel<128><<<grid, 128, smem, s>>>(tt, colour, step, status, stage_words, wait_limit, extra_tx);
+        launch_nt<128>(tt, one, colour, step, status, grid, smem, stage_words, s, wait_limit, extra_tx);
         break;
     case 256:
-        packed_half_sweep_kernel<256><<<grid, 256, smem, s>>>(tt, colour, step, status, stage_words, wait_limit, extra_tx);
+        launch_nt<256>(tt, one, colour, step, status, grid, smem, stage_words, s, wait_limit, extra_tx);
         break;
     case 512:
-        packed_half_sweep_kernel<512><<<grid, 512, smem, s>>>(tt, colour, step, status, stage_words, wait_limit, extra_tx);
+        launch_nt<512>(tt, one, colour, step, status, grid, smem, stage_words, s, wait_limit, extra_tx);
         break;
     default:
         return cudaErrorInvalidValue;
@@ -365,18 +406,25 @@ cudaError_t launch_packed_half_sweep(const TileTable& tt, int colour, int step, 
     return cudaGetLastError();
 }
 
+template <int NT>
+cudaError_t set_limit_nt(size_t bytes)
+{
+    cudaError_t e = cudaFuncSetAttribute(packed_half_sweep_kernel<NT, false>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(packed_half_sweep_kernel<NT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)bytes);
+}
+
 cudaError_t packed_set_smem_limit(int threads, size_t bytes)
 {
     switch (threads) {
     case 128:
-        return cudaFuncSetAttribute(packed_half_sweep_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)bytes);
+        return set_limit_nt<128>(bytes);
     case 256:
-        return cudaFuncSetAttribute(packed_half_sweep_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)bytes);
+        return set_limit_nt<256>(bytes);
     case 512:
-        return cudaFuncSetAttribute(packed_half_sweep_kernel<512>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)bytes);
+        return set_limit_nt<512>(bytes);
     default:
         return cudaErrorInvalidValue;
     }
@@ -386,11 +434,14 @@ cudaError_t packed_occupancy(int threads, size_t smem, int* blocks_per_sm)
 {
     switch (threads) {
     case 128:
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, packed_half_sweep_kernel<128>, 128, smem);
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, packed_half_sweep_kernel<128, false>, 128,
+                                                             smem);
     case 256:
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, packed_half_sweep_kernel<256>, 256, smem);
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, packed_half_sweep_kernel<256, false>, 256,
+                                                             smem);
     case 512:
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, packed_half_sweep_kernel<512>, 512, smem);
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, packed_half_sweep_kernel<512, false>, 512,
+                                                             smem);
     default:
         return cudaErrorInvalidValue;
     }
