@@ -186,15 +186,18 @@ __device__ __forceinline__ uint32_t update_word(uint32_t t, uint32_t up, uint32_
 
     uint32_t x[32];
     philox_word8(q_lo, pc, key, x);
-    // compare bits gathered in four independent partial masks (short OR chains)
-    uint32_t q2p[4] = {0, 0, 0, 0}, q4p[4] = {0, 0, 0, 0};
+    // Threshold tests as carry chains: sub.cc sets the carry flag iff x >= t (no
+    // borrow), and addc doubles the mask and adds that flag, so after 32 steps bit b
+    // of g holds [x[b] >= t]; two instructions per compare, no predicate-to-bit
+    // packing.  q = ~g is the mask of x < t.
+    uint32_t g2 = 0, g4 = 0;
 #pragma unroll
-    for (int b = 0; b < 32; ++b) {
-        q2p[b & 3] |= (x[b] < t2 ? 1u : 0u) << b;
-        q4p[b & 3] |= (x[b] < t4 ? 1u : 0u) << b;
+    for (int b = 31; b >= 0; --b) {
+        asm("{\n\t.reg .u32 d;\n\tsub.cc.u32 d, %1, %2;\n\taddc.u32 %0, %0, %0;\n\t}" : "+r"(g2) : "r"(x[b]), "r"(t2));
+        asm("{\n\t.reg .u32 d;\n\tsub.cc.u32 d, %1, %2;\n\taddc.u32 %0, %0, %0;\n\t}" : "+r"(g4) : "r"(x[b]), "r"(t4));
     }
-    const uint32_t q2 = all2 | q2p[0] | q2p[1] | q2p[2] | q2p[3];
-    const uint32_t q4 = all4 | q4p[0] | q4p[1] | q4p[2] | q4p[3];
+    const uint32_t q2 = all2 | ~g2;
+    const uint32_t q4 = all4 | ~g4;
     // n_anti >= 2 (h <= 0): always; n_anti == 1 (h = 2): x < T2; n_anti == 0 (h = 4):
     // x < T4.  T4 <= T2, so q4 is a subset of q2 and ORing q4 everywhere is exact.
     const uint32_t flip = b1 | b2 | (b0 & q2) | q4;
