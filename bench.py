@@ -316,6 +316,53 @@ def run_batched(args, which: str) -> None:
                       "note": f"plain = each lattice alone with its own launches, {n_plain} sweeps each"}))
 
 
+def run_binder(args) -> None:
+    """Physics validation: U4(T) and <|m|>(T) for L = 64..512 from one batch; the
+    curves of different L cross near T_c (the paper's Fig. 3, reduced)."""
+    import numpy as np
+    import torch
+
+    from paper_1903_11714_gb300 import ising, workloads
+
+    sweeps = args.binder_sweeps
+    burn = sweeps // 10
+    lats = workloads.binder_scan(sweeps)
+    st = torch.cuda.Stream()
+    arena = sum(l.L * l.L // 8 + 16 * l.sweeps + 4096 for l in lats)
+    b = ising.Batch(len(lats), max(workloads.BINDER_LS), arena, 0, stream=st)
+    idx = [b.add(l.L, l.beta, l.seed, l.start, l.sweeps) for l in lats]
+    graph = 1000 if sweeps % 1000 == 0 else 0
+    e0, e1 = _events(torch, st)
+    e0.record(st)
+    b.run(sweeps, graph_sweeps=graph)
+    e1.record(st)
+    torch.cuda.synchronize()
+    b.synchronize()
+    ms = e0.elapsed_time(e1)
+    table = {}
+    for l, i in zip(lats, idx):
+        m = b.moments(i, burn)
+        table.setdefault(l.L, []).append((workloads.BETA_C_EXACT / l.beta, m["binder"], m["abs_m"], m["e"]))
+    b.close()
+    # crossings of U4(T) between consecutive sizes (linear interpolation of the difference)
+    crossings = {}
+    Ls = sorted(table)
+    for L1, L2 in zip(Ls, Ls[1:]):
+        a = sorted(table[L1])
+        c = sorted(table[L2])
+        d = [(p[0], p[1] - q[1]) for p, q in zip(a, c)]
+        for (t0, d0), (t1, d1) in zip(d, d[1:]):
+            if d0 * d1 <= 0 and d0 != d1:
+                crossings[f"{L1}-{L2}"] = t0 + (t1 - t0) * d0 / (d0 - d1)
+                break
+    flips = sweeps * sum(l.L * l.L for l in lats)
+    print(json.dumps({"metric": "Binder-parameter scan: U4 and <|m|> vs T/Tc", "workload": "binder",
+                      "unit": UNIT, "value": flips / (ms * 1e6), "sweeps": sweeps, "burn_in": burn,
+                      "crossing_T_over_Tc": crossings,
+                      "U4": {str(L): [[round(t, 4), u] for t, u, _, _ in sorted(v)] for L, v in table.items()},
+                      "abs_m": {str(L): [[round(t, 4), m] for t, _, m, _ in sorted(v)] for L, v in table.items()}}))
+
+
 def run_serve(args) -> None:
     """Poisson arrivals at ~80 % of measured capacity; p50/p99 latency."""
     import torch
@@ -357,8 +404,9 @@ def main() -> None:
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--ref-rows", type=int, default=1024)
-    ap.add_argument("--workload", choices=["single_large", "single_small", "scan", "uneven", "serve"],
+    ap.add_argument("--workload", choices=["single_large", "single_small", "scan", "uneven", "serve", "binder"],
                     default="single_large")
+    ap.add_argument("--binder-sweeps", type=int, default=1_000_000)
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--serve-calib", type=int, default=150)
     ap.add_argument("--serve-slots", type=int, default=256)
@@ -381,7 +429,7 @@ def main() -> None:
     torch.cuda.set_device(local)
     if args.workload != "single_large":
         libbuild.build()
-        {"single_small": run_single_small, "serve": run_serve}.get(
+        {"single_small": run_single_small, "serve": run_serve, "binder": run_binder}.get(
             args.workload, lambda a: run_batched(a, args.workload))(args)
         return
     dist = None

@@ -55,6 +55,25 @@ TEMPERATURE_SCAN_BURN_IN = 500
 TEMPERATURE_SCAN_GRAPH_SWEEPS = 100
 
 
+# Binder-parameter scan (a reduced form of the paper's Fig. 3): U4 and <|m|> against
+# T/T_c for several L; 10^6 samples per point with the first 10^5 discarded, as in
+# the figure's caption.
+BINDER_LS = (64, 128, 256, 512)
+BINDER_T_OVER_TC = (0.90, 0.94, 0.97, 0.99, 1.00, 1.01, 1.03, 1.06, 1.10)
+BINDER_SWEEPS = 1_000_000
+BINDER_BURN_IN = 100_000
+BETA_C_EXACT = 0.5 * math.log(1.0 + math.sqrt(2.0))
+
+
+def binder_scan(sweeps: int = BINDER_SWEEPS) -> list[Lattice]:
+    """One lattice per (L, T/T_c): beta = beta_c / (T/T_c), cold start, seed from (L, k)."""
+    out = []
+    for L in BINDER_LS:
+        for k, t in enumerate(BINDER_T_OVER_TC):
+            out.append(Lattice(L=L, beta=BETA_C_EXACT / t, seed=7_000_000 + 100 * L + k, start=COLD, sweeps=sweeps))
+    return out
+
+
 def _uneven_path() -> str:
     return os.path.join(_HERE, "configs", "uneven_batch_200.json")
 
