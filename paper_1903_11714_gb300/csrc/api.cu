@@ -608,7 +608,17 @@ int ising_sweep(ising_t h, int64_t n)
     if (n == 0) return ISING_OK;
     rc = ensure_hist(h, h->sweeps_done + n);
     if (rc) return rc;
-    if (h->kernel == ISING_PACKED) {
+    if (h->kernel == ISING_PACKED && h->L <= packed_resident_max_L()) {
+        // small lattice: one CTA keeps both planes on chip for many sweeps per launch
+        LatticeDesc d = h->desc;
+        for (int64_t done = 0; done < n;) {
+            const int64_t chunk = std::min<int64_t>(n - done, 4096);
+            d.sweep = (uint32_t)(h->sweeps_done + done);
+            cudaError_t e = launch_packed_resident(d, (int)chunk, h->stream);
+            if (e != cudaSuccess) return cuda_fail(e, "resident sweep launch");
+            done += chunk;
+        }
+    } else if (h->kernel == ISING_PACKED) {
         rc = h->eng.run(n, 0);
         if (rc) return rc;
     } else {

@@ -57,6 +57,10 @@ cudaError_t launch_packed_half_sweep(const TileTable& tt, int colour, int step, 
                                      int threads, int smem_stage_bytes, cudaStream_t s,
                                      long long wait_limit = kWaitLimitCycles, uint32_t extra_tx = 0,
                                      const LatticeDesc* one = nullptr);
+// One small lattice (L <= packed_resident_max_L()) swept nsweeps times by a single
+// CTA holding both planes in shared memory; writes hist[d.sweep .. +nsweeps).
+int packed_resident_max_L();
+cudaError_t launch_packed_resident(const LatticeDesc& d, int nsweeps, cudaStream_t s);
 cudaError_t launch_packed_advance(LatticeDesc* desc, const int32_t* count, int max_count, int steps,
                                   cudaStream_t s);
 cudaError_t launch_packed_init(uint32_t* black, uint32_t* white, int64_t L, uint64_t key, int start,

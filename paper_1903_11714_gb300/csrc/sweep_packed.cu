@@ -313,6 +313,106 @@ __global__ void __launch_bounds__(NT, (ISING_SWEEP_THREADS_PER_SM / NT > 0 ? ISI
             const bool q_small = L <= 131072;
             const PhiloxWordConsts pc_tile = philox_consts(key, 0u, sweep, (uint32_t)colour);
             const int nwords = TR * W;
+            // Four (or two) adjacent words per thread and iteration: one 128-bit (or
+            // 64-bit) shared-memory load per neighbour row and one global store, and
+            // one index step, per group of words.
+            if ((W & 3) == 0) {
+                const int W4 = W >> 2, nquads = nwords >> 2;
+                const int step_r = NT / W4, step_w = NT - step_r * W4;
+                int r = tid / W4, w4 = tid - r * W4;
+                for (int idx4 = tid; idx4 < nquads; idx4 += NT) {
+                    const int i = i0 + r;
+                    const int w = 4 * w4;
+                    const uint32_t* srow = s_src + (size_t)(HB + r) * W;
+                    const uint4 upq = *reinterpret_cast<const uint4*>(srow + w - W);
+                    const uint4 dnq = *reinterpret_cast<const uint4*>(srow + w + W);
+                    const uint4 smq = *reinterpret_cast<const uint4*>(srow + w);
+                    const uint4 tgq = *reinterpret_cast<const uint4*>(s_tgt + (size_t)r * W + w);
+                    const int par = (i + colour) & 1;
+                    uint32_t hz[4];
+                    if (par) {
+                        const uint32_t nextw = srow[(w + 4 == W) ? 0 : w + 4];
+                        hz[0] = __funnelshift_r(smq.x, smq.y, 1);
+                        hz[1] = __funnelshift_r(smq.y, smq.z, 1);
+                        hz[2] = __funnelshift_r(smq.z, smq.w, 1);
+                        hz[3] = __funnelshift_r(smq.w, nextw, 1);
+                    } else {
+                        const uint32_t prevw = srow[(w == 0) ? W - 1 : w - 1];
+                        hz[0] = __funnelshift_l(prevw, smq.x, 1);
+                        hz[1] = __funnelshift_l(smq.x, smq.y, 1);
+                        hz[2] = __funnelshift_l(smq.y, smq.z, 1);
+                        hz[3] = __funnelshift_l(smq.z, smq.w, 1);
+                    }
+                    const uint64_t q0 = (uint64_t)i * (uint64_t)(L >> 3) + 8ull * (uint64_t)w;
+                    const PhiloxWordConsts pc =
+                        q_small ? pc_tile : philox_consts(key, (uint32_t)(q0 >> 32), sweep, (uint32_t)colour);
+                    const uint32_t up[4] = {upq.x, upq.y, upq.z, upq.w}, dn[4] = {dnq.x, dnq.y, dnq.z, dnq.w};
+                    const uint32_t sm[4] = {smq.x, smq.y, smq.z, smq.w}, tg[4] = {tgq.x, tgq.y, tgq.z, tgq.w};
+                    uint32_t nw[4];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k)
+                        nw[k] = update_word(tg[k], up[k], dn[k], sm[k], hz[k], (uint32_t)q0 + 8u * k, pc, key, t2, t4,
+                                            all2, all4);
+                    *reinterpret_cast<uint4*>(out_plane + (size_t)i * W + w) = make_uint4(nw[0], nw[1], nw[2], nw[3]);
+                    if (colour == 1) {
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            ups += __popc(nw[k]) + __popc(sm[k]);
+                            anti += __popc(nw[k] ^ up[k]) + __popc(nw[k] ^ dn[k]) + __popc(nw[k] ^ sm[k]) +
+                                    __popc(nw[k] ^ hz[k]);
+                        }
+                    }
+                    r += step_r;
+                    w4 += step_w;
+                    if (w4 >= W4) {
+                        w4 -= W4;
+                        ++r;
+                    }
+                }
+            } else if ((W & 1) == 0) {
+                // pairs of adjacent words (W even but not a multiple of 4)
+                const int W2 = W >> 1, npairs = nwords >> 1;
+                const int step_r = NT / W2, step_w = NT - step_r * W2;
+                int r = tid / W2, w2 = tid - r * W2;
+                for (int idx2 = tid; idx2 < npairs; idx2 += NT) {
+                    const int i = i0 + r;
+                    const int w = 2 * w2;
+                    const uint32_t* srow = s_src + (size_t)(HB + r) * W;
+                    const uint2 upp = *reinterpret_cast<const uint2*>(srow + w - W);
+                    const uint2 dnp = *reinterpret_cast<const uint2*>(srow + w + W);
+                    const uint2 smp = *reinterpret_cast<const uint2*>(srow + w);
+                    const uint2 tgp = *reinterpret_cast<const uint2*>(s_tgt + (size_t)r * W + w);
+                    const int par = (i + colour) & 1;
+                    uint32_t hz0, hz1;
+                    if (par) {
+                        const uint32_t nextw = srow[(w + 2 == W) ? 0 : w + 2];
+                        hz0 = __funnelshift_r(smp.x, smp.y, 1);
+                        hz1 = __funnelshift_r(smp.y, nextw, 1);
+                    } else {
+                        const uint32_t prevw = srow[(w == 0) ? W - 1 : w - 1];
+                        hz0 = __funnelshift_l(prevw, smp.x, 1);
+                        hz1 = __funnelshift_l(smp.x, smp.y, 1);
+                    }
+                    const uint64_t q0 = (uint64_t)i * (uint64_t)(L >> 3) + 8ull * (uint64_t)w;
+                    const PhiloxWordConsts pc =
+                        q_small ? pc_tile : philox_consts(key, (uint32_t)(q0 >> 32), sweep, (uint32_t)colour);
+                    uint2 nw;
+                    nw.x = update_word(tgp.x, upp.x, dnp.x, smp.x, hz0, (uint32_t)q0, pc, key, t2, t4, all2, all4);
+                    nw.y = update_word(tgp.y, upp.y, dnp.y, smp.y, hz1, (uint32_t)q0 + 8u, pc, key, t2, t4, all2, all4);
+                    *reinterpret_cast<uint2*>(out_plane + (size_t)i * W + w) = nw;
+                    if (colour == 1) {
+                        ups += __popc(nw.x) + __popc(smp.x) + __popc(nw.y) + __popc(smp.y);
+                        anti += __popc(nw.x ^ upp.x) + __popc(nw.x ^ dnp.x) + __popc(nw.x ^ smp.x) + __popc(nw.x ^ hz0)
+                              + __popc(nw.y ^ upp.y) + __popc(nw.y ^ dnp.y) + __popc(nw.y ^ smp.y) + __popc(nw.y ^ hz1);
+                    }
+                    r += step_r;
+                    w2 += step_w;
+                    if (w2 >= W2) {
+                        w2 -= W2;
+                        ++r;
+                    }
+                }
+            } else {
             // (row, word) of idx = tid + k*NT, advanced without a division per word
             const int step_r = NT / W, step_w = NT - step_r * W;
             int r = tid / W, w = tid - r * W;
@@ -349,11 +449,86 @@ __global__ void __launch_bounds__(NT, (ISING_SWEEP_THREADS_PER_SM / NT > 0 ? ISI
                 }
             }
         }
+            }
         __syncthreads();
         buf ^= 1;
         cur = nxt;
     }
     if (colour == 1 && acc_lat >= 0) flush(acc_lat);
+}
+
+// Resident form for one small lattice: both planes live in this CTA's shared
+// memory for `nsweeps` sweeps, with a block barrier between half-sweeps instead
+// of a kernel launch.  Same words, neighbours, draws and decisions as the tiled
+// kernel; the white pass writes (M, E) of each sweep straight into the history.
+template <int NT>
+__global__ void __launch_bounds__(NT, 1) packed_resident_kernel(const __grid_constant__ LatticeDesc d, int nsweeps)
+{
+    extern __shared__ __align__(16) uint32_t planes_s[];
+    __shared__ uint32_t red[2 * (NT / 32)];
+    const int W = d.W, L = d.L;
+    const int words = L * W;
+    uint32_t* pl[2] = {planes_s, planes_s + words};
+    const int tid = threadIdx.x;
+    for (int k = tid; k < words; k += NT) {
+        pl[0][k] = d.plane[0][k];
+        pl[1][k] = d.plane[1][k];
+    }
+    __syncthreads();
+    const uint64_t key = d.key;
+    const bool q_small = L <= 131072;
+    for (int s = 0; s < nsweeps; ++s) {
+        const uint32_t sweep = d.sweep + (uint32_t)s;
+        for (int colour = 0; colour < 2; ++colour) {
+            const uint32_t* src = pl[colour ^ 1];
+            uint32_t* tgt = pl[colour];
+            const PhiloxWordConsts pc_all = philox_consts(key, 0u, sweep, (uint32_t)colour);
+            uint32_t ups = 0, anti = 0;
+            for (int idx = tid; idx < words; idx += NT) {
+                const int i = idx / W, w = idx - i * W;
+                const int iu = i == 0 ? L - 1 : i - 1, id = i + 1 == L ? 0 : i + 1;
+                const uint32_t up = src[iu * W + w], down = src[id * W + w], same = src[idx];
+                uint32_t hz;
+                if ((i + colour) & 1)
+                    hz = __funnelshift_r(same, src[i * W + (w + 1 == W ? 0 : w + 1)], 1);
+                else
+                    hz = __funnelshift_l(src[i * W + (w == 0 ? W - 1 : w - 1)], same, 1);
+                const uint64_t q0 = (uint64_t)i * (uint64_t)(L >> 3) + 8ull * (uint64_t)w;
+                const PhiloxWordConsts pc =
+                    q_small ? pc_all : philox_consts(key, (uint32_t)(q0 >> 32), sweep, (uint32_t)colour);
+                const uint32_t nw =
+                    update_word(tgt[idx], up, down, same, hz, (uint32_t)q0, pc, key, d.t2, d.t4, d.all2, d.all4);
+                tgt[idx] = nw;
+                if (colour == 1) {
+                    ups += __popc(nw) + __popc(same);
+                    anti += __popc(nw ^ up) + __popc(nw ^ down) + __popc(nw ^ same) + __popc(nw ^ hz);
+                }
+            }
+            if (colour == 1) {
+                const uint32_t u = __reduce_add_sync(0xffffffffu, ups);
+                const uint32_t a = __reduce_add_sync(0xffffffffu, anti);
+                if ((tid & 31) == 0) {
+                    red[2 * (tid >> 5)] = u;
+                    red[2 * (tid >> 5) + 1] = a;
+                }
+            }
+            __syncthreads();
+            if (colour == 1 && tid == 0) {
+                int64_t su = 0, sa = 0;
+                for (int k = 0; k < NT / 32; ++k) {
+                    su += red[2 * k];
+                    sa += red[2 * k + 1];
+                }
+                const int64_t N = (int64_t)L * L;
+                d.hist[2 * (int64_t)sweep] = 2 * su - N;
+                d.hist[2 * (int64_t)sweep + 1] = 2 * sa - 2 * N;
+            }
+        }
+    }
+    for (int k = tid; k < words; k += NT) {
+        d.plane[0][k] = pl[0][k];
+        d.plane[1][k] = pl[1][k];
+    }
 }
 
 // After `steps` sweeps: advance each live lattice's sweep counter (bounded by its target).
@@ -448,6 +623,22 @@ cudaError_t packed_occupancy(int threads, size_t smem, int* blocks_per_sm)
     default:
         return cudaErrorInvalidValue;
     }
+}
+
+int packed_resident_max_L() { return 256; }
+
+cudaError_t launch_packed_resident(const LatticeDesc& d, int nsweeps, cudaStream_t s)
+{
+    const size_t smem = sizeof(uint32_t) * 2 * (size_t)d.L * (size_t)d.W;
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(packed_resident_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)(sizeof(uint32_t) * 2 * 256 * 4));
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    packed_resident_kernel<256><<<1, 256, smem, s>>>(d, nsweeps);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_packed_advance(LatticeDesc* desc, const int32_t* count, int max_count, int steps, cudaStream_t s)

@@ -82,6 +82,7 @@ def test_single_small_matches_golden():
     (192, 0.6, 13, 1, 20),        # W = 3: not a multiple of 4
     (256, BC, 14, 0, 15),         # W = 4: single-row halos
     (320, 0.45, 15, 0, 12),       # W = 5
+    (384, 0.41, 18, 0, 10),       # W = 6: word pairs
     (512, 0.5, 16, 1, 10),
     (1024, BC, 17, 0, 6),
     (2048, 0.35, 0xFFFFFFFFFFFFFFFF, 0, 3),
@@ -107,6 +108,23 @@ def test_int8_matches_oracle(L, beta, seed, start, sweeps):
 def test_degenerate_temperatures(kernel, beta):
     # beta = 0: T = 2^32, every proposal flips; beta = 200: T = 0, zero-temperature dynamics
     assert_chain_equal(128, beta, 5, 0, 8, kernel)
+
+
+@pytest.mark.parametrize("L", [64, 128, 192, 256])
+def test_resident_small_lattice_equals_tiled_batch(L):
+    """Single handles of L <= 256 keep the lattice in one CTA's shared memory; the
+    batch runs the same lattice through the tiled kernel.  Same chain."""
+    beta, seed, sweeps = 0.43, 40 + L, 300
+    a = ising.Lattice(L, beta, seed, ising.HOT).sweep(sweeps)
+    b = ising.Batch(1, L, L * L // 8 + 16 * sweeps + 4096)
+    i = b.add(L, beta, seed, ising.HOT, sweeps)
+    b.run(sweeps)
+    Ma, Ea = a.history()
+    Mb, Eb = b.history(i)
+    assert np.array_equal(Ma, Mb) and np.array_equal(Ea, Eb)
+    assert np.array_equal(a.get_lattice(), b.get_lattice(i))
+    a.close()
+    b.close()
 
 
 def test_packed_and_int8_agree_mid_size():
