@@ -3,9 +3,10 @@
 // the same Philox keying, integer thresholds and fused M/E counts as the
 // bit-packed kernel, so both reach the same chain bit for bit.
 //
-// One thread owns an 8-byte chunk of a row (columns 8g .. 8g+7).  The four
-// target-colour sites in it, j = 8g + 2b + r with r = (i + c) & 1, have plane
-// indices p = i*L/2 + 4g + b and so share one Philox call (q = i*L/8 + g).
+// The start-state kernel works on 8-byte chunks (columns 8g .. 8g+7): the four
+// sites of each colour in a chunk share one Philox call (q = i*L/8 + g).  The
+// half-sweep works on 64-byte row segments (32 target sites, 8 interleaved calls)
+// when L % 64 == 0, else on 8-byte chunks.
 #include "ising_internal.cuh"
 #include "philox.cuh"
 
@@ -45,6 +46,11 @@ __global__ void int8_init_kernel(int8_t* lat, int64_t L, uint64_t key, int start
     }
 }
 
+__device__ __forceinline__ int sbyte32(uint32_t v, int k)
+{
+    return (int)(int8_t)(uint8_t)(v >> (8 * k));
+}
+
 __device__ __forceinline__ void block_add_pair(long long a, long long b, int64_t* slot)
 {
     __shared__ long long red[2][32];
@@ -69,7 +75,94 @@ __device__ __forceinline__ void block_add_pair(long long a, long long b, int64_t
     }
 }
 
-__global__ void int8_half_sweep_kernel(int8_t* lat, int64_t L, uint64_t key, uint32_t t2, uint32_t t4, uint32_t all2,
+__global__ void int8_half_sweep_seg64_kernel(int8_t* lat, int64_t L, uint64_t key, uint32_t t2, uint32_t t4, uint32_t all2,
+                                       uint32_t all4, uint32_t sweep, int colour, int64_t* hist_slot)
+{
+    // One thread owns a 64-byte segment of a row: columns 64g .. 64g+63, i.e. the
+    // 32 target sites j = 64g + 2b + r (b = 0..31) whose plane indices p = i*L/2 +
+    // 32g + b are served by the eight Philox calls q = i*L/8 + 8g + b/4.
+    const int64_t G = L / 64;
+    const int64_t segs = L * G;
+    if (colour == 0 && blockIdx.x == 0 && threadIdx.x == 0) {
+        hist_slot[0] = 0;  // opened here, filled by the colour-1 pass of the same sweep
+        hist_slot[1] = 0;
+    }
+    const PhiloxWordConsts pc = philox_consts(key, 0u, sweep, (uint32_t)colour);
+    long long m_acc = 0, e_acc = 0;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < segs;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = idx / G, g = idx - i * G;
+        const int64_t iu = i == 0 ? L - 1 : i - 1, id = i + 1 == L ? 0 : i + 1;
+        const int r = (int)((i + colour) & 1);
+        int8_t* row = lat + i * L + 64 * g;
+        uint32_t cw[16], uw[16], dw[16];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const uint4 c4 = reinterpret_cast<const uint4*>(row)[k];
+            const uint4 u4 = reinterpret_cast<const uint4*>(lat + iu * L + 64 * g)[k];
+            const uint4 d4 = reinterpret_cast<const uint4*>(lat + id * L + 64 * g)[k];
+            cw[4 * k] = c4.x; cw[4 * k + 1] = c4.y; cw[4 * k + 2] = c4.z; cw[4 * k + 3] = c4.w;
+            uw[4 * k] = u4.x; uw[4 * k + 1] = u4.y; uw[4 * k + 2] = u4.z; uw[4 * k + 3] = u4.w;
+            dw[4 * k] = d4.x; dw[4 * k + 1] = d4.y; dw[4 * k + 2] = d4.z; dw[4 * k + 3] = d4.w;
+        }
+        // the one neighbour outside the segment: column 64g-1 (r = 0) or 64g+64 (r = 1)
+        const int64_t edge_col = r ? (g + 1 == G ? 0 : 64 * g + 64) : (g == 0 ? L - 1 : 64 * g - 1);
+        const int edge = lat[i * L + edge_col];
+        const uint64_t q0 = (uint64_t)i * (uint64_t)(L / 8) + 8ull * (uint64_t)g;
+        const PhiloxWordConsts pcw =
+            L <= 131072 ? pc : philox_consts(key, (uint32_t)(q0 >> 32), sweep, (uint32_t)colour);
+        uint32_t x[32];
+        philox_word8((uint32_t)q0, pcw, key, x);
+        // threshold tests of the 32 draws (carry flag set iff x >= t)
+        uint32_t g2 = 0, g4 = 0;
+#pragma unroll
+        for (int b = 31; b >= 0; --b) {
+            asm("{\n\t.reg .u32 d;\n\tsub.cc.u32 d, %1, %2;\n\taddc.u32 %0, %0, %0;\n\t}" : "+r"(g2) : "r"(x[b]), "r"(t2));
+            asm("{\n\t.reg .u32 d;\n\tsub.cc.u32 d, %1, %2;\n\taddc.u32 %0, %0, %0;\n\t}" : "+r"(g4) : "r"(x[b]), "r"(t4));
+        }
+        const uint32_t q2 = all2 | ~g2, q4 = all4 | ~g4;
+        uint32_t nw[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) nw[k] = cw[k];
+        long long e_here = 0;
+        // both parities are unrolled; r picks the target bytes (k = 2b + r)
+#pragma unroll
+        for (int rr = 0; rr < 2; ++rr) {
+            if (rr != r) continue;
+#pragma unroll
+            for (int b = 0; b < 32; ++b) {
+                const int k = 2 * b + rr;
+                const int s = sbyte32(cw[k >> 2], k & 3);
+                const int left = k == 0 ? edge : sbyte32(cw[(k - 1) >> 2], (k - 1) & 3);
+                const int right = k == 63 ? edge : sbyte32(cw[(k + 1) >> 2], (k + 1) & 3);
+                const int nn = sbyte32(uw[k >> 2], k & 3) + sbyte32(dw[k >> 2], k & 3) + left + right;
+                const int h = s * nn;
+                const bool acc = h <= 0 || (h == 2 ? ((q2 >> b) & 1u) : ((q4 >> b) & 1u));
+                if (acc) nw[k >> 2] ^= 0xFEu << (8 * (k & 3));  // 0x01 <-> 0xFF
+                e_here -= (long long)(acc ? -s : s) * nn;
+            }
+        }
+        bool changed = false;
+#pragma unroll
+        for (int k = 0; k < 16; ++k) changed |= nw[k] != cw[k];
+        if (changed) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                reinterpret_cast<uint4*>(row)[k] = make_uint4(nw[4 * k], nw[4 * k + 1], nw[4 * k + 2], nw[4 * k + 3]);
+        }
+        if (colour == 1) {
+            long long msum = 0;
+#pragma unroll
+            for (int k = 0; k < 64; ++k) msum += sbyte32(nw[k >> 2], k & 3);
+            m_acc += msum;
+            e_acc += e_here;
+        }
+    }
+    if (colour == 1) block_add_pair(m_acc, e_acc, hist_slot);
+}
+
+// L % 64 != 0: one thread per 8-byte chunk (4 target sites, one Philox call).
+__global__ void int8_half_sweep_chunk8_kernel(int8_t* lat, int64_t L, uint64_t key, uint32_t t2, uint32_t t4, uint32_t all2,
                                        uint32_t all4, uint32_t sweep, int colour, int64_t* hist_slot)
 {
     const int64_t G = L / 8;
@@ -165,8 +258,12 @@ cudaError_t launch_int8_init(int8_t* lat, int64_t L, uint64_t key, int start, cu
 cudaError_t launch_int8_half_sweep(int8_t* lat, int64_t L, uint64_t key, uint32_t t2, uint32_t t4, uint32_t all2,
                                    uint32_t all4, uint32_t sweep, int colour, int64_t* hist_slot, cudaStream_t s)
 {
-    int8_half_sweep_kernel<<<grid_cap(L * (L / 8), 256, 8), 256, 0, s>>>(lat, L, key, t2, t4, all2, all4, sweep,
-                                                                        colour, hist_slot);
+    if (L % 64 == 0)
+        int8_half_sweep_seg64_kernel<<<grid_cap(L * (L / 64), 256, 8), 256, 0, s>>>(lat, L, key, t2, t4, all2, all4,
+                                                                                  sweep, colour, hist_slot);
+    else
+        int8_half_sweep_chunk8_kernel<<<grid_cap(L * (L / 8), 256, 8), 256, 0, s>>>(lat, L, key, t2, t4, all2, all4,
+                                                                                   sweep, colour, hist_slot);
     return cudaGetLastError();
 }
 
