@@ -31,19 +31,19 @@ sys.path.insert(0, ROOT)
 
 METRIC = "spin-flip attempts/ns on 1 GB300 (bit-packed checkerboard sweep, bit-exact)"
 UNIT = "flips/ns"
-# Algorithmic integer work per site update.  A Philox4x32-10 call serves 4 sites:
-# 10 rounds of two 32x32->64 products and two three-input XORs; the round-1 and
-# round-2 products and one XOR that do not depend on the site are formed once per
-# 32-site word, leaving 18 products + 19 XORs = 37 operations per call, 9.25 per
-# site.  The acceptance test is 2 threshold compares per site; counting the
-# anti-aligned neighbours and forming the flip mask is ~12 bitwise operations per
-# 32 sites (0.375 per site).
+# Algorithmic work per site update.  A Philox4x32-10 call serves 4 sites with 10
+# rounds of two 32x32->64 products and two three-input XORs; the round-1 and
+# round-2 products (and one XOR) that do not depend on the site are formed once per
+# 32-site word, leaving 18 products + 19 XORs per call: 4.5 products and 4.75 XORs
+# per site.  The acceptance test adds 2 threshold compares per site and the
+# neighbour count / flip mask ~12 bitwise operations per 32 sites.
 MULS_PER_SITE_SWEEP = 4.5
-INT_OPS_PER_SITE = 9.25 + 2.0 + 0.375
-# Integer datapath: 16 INT32 lanes per scheduler, 4 schedulers per SM, shared by
-# multiplies (IMAD) and logic / compare / add instructions -> 64 integer
-# operations per clock per SM (the ALU probe measures 64.0).
-INT_OPS_PER_CLK_SM = 64.0
+ALU_OPS_PER_SITE = 4.75 + 2.0 + 0.375
+# Integer multiply pipe: 16 lanes per scheduler, 4 schedulers per SM, a 32x32->64
+# product taking two lane-cycles -> 32 products per clock per SM.  Logic and
+# compare instructions run on the ALU pipe: 64 per clock per SM.
+MULS_PER_CLK_SM = 32.0
+ALU_OPS_PER_CLK_SM = 64.0
 N_SMS = 152
 # algorithmic bytes per site per sweep (packed): each half-sweep reads the target
 # and source planes and writes the target plane, N/2 bits each
@@ -475,20 +475,21 @@ def main() -> None:
     # dominant kernel: the packed half-sweep (2 launches per sweep + 1 counter advance per call)
     launches = 2 * args.steps + 1
     t_launch_s = ms * 1e-3 / (2 * args.steps)
-    ops_per_launch = INT_OPS_PER_SITE * N / 2
-    achieved = ops_per_launch / t_launch_s / 1e12
-    peak = INT_OPS_PER_CLK_SM * N_SMS * sm_max * 1e6 / 1e12
-    muls_achieved = MULS_PER_SITE_SWEEP * N / 2 / t_launch_s / 1e12
-    # packed: 3 planes of N/2 bits per half-sweep; int8: the whole lattice read and written
+    muls_per_launch = MULS_PER_SITE_SWEEP * N / 2
+    achieved = muls_per_launch / t_launch_s / 1e12
+    peak = MULS_PER_CLK_SM * N_SMS * sm_max * 1e6 / 1e12
+    alu_achieved = ALU_OPS_PER_SITE * N / 2 / t_launch_s / 1e12
     bytes_per_launch = BYTES_PER_SITE_SWEEP * N / 2 if kernel == ising.PACKED else 2.0 * N
     traffic = committed_traffic(L) if kernel == ising.PACKED else None
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tintop/s", "frac": achieved / peak,
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tmul/s", "frac": achieved / peak,
                 "traffic": traffic,
-                "peak_basis": f"{INT_OPS_PER_CLK_SM:.0f} integer ops/clk/SM (16 INT32 lanes x 4 schedulers, shared by "
-                              f"IMAD and logic ops) x {N_SMS} SMs x {sm_max:.0f} MHz; achieved counts "
-                              f"{INT_OPS_PER_SITE} algorithmic integer ops per site update",
-                "probe_int_ops_per_clk_sm": alu_per_clk, "probe_mul_xor_steps_per_clk_sm": mul_per_clk,
-                "mul_view": {"achieved_tmul_s": muls_achieved, "peak_tmul_s": 32.0 * N_SMS * sm_max * 1e6 / 1e12},
+                "peak_basis": f"integer multiply pipe: {MULS_PER_CLK_SM:.0f} 32x32->64 products/clk/SM (16 lanes x 4 "
+                              f"schedulers, 2 lane-cycles each) x {N_SMS} SMs x {sm_max:.0f} MHz; achieved counts "
+                              f"{MULS_PER_SITE_SWEEP} Philox products per site update",
+                "probe_mul_xor_steps_per_clk_sm": mul_per_clk, "probe_alu_ops_per_clk_sm": alu_per_clk,
+                "alu_view": {"achieved_tops": alu_achieved,
+                             "peak_tops": ALU_OPS_PER_CLK_SM * N_SMS * sm_max * 1e6 / 1e12,
+                             "ops_per_site": ALU_OPS_PER_SITE},
                 "hbm_achieved_gbs": bytes_per_launch / t_launch_s / 1e9,
                 "hbm_peak_gbs": peaks.get("hbm_gbs", 6800.0)}
 
