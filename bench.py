@@ -141,7 +141,7 @@ def measured_peaks() -> dict:
 
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for f in ("sweep_packed.cu", "philox.cuh", "ising_internal.cuh"):
+    for f in ("sweep_packed.cu", "word_update.cuh", "philox.cuh", "ising_internal.cuh"):
         with open(os.path.join(ROOT, "paper_1903_11714_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

@@ -176,8 +176,9 @@ int ising_batch_create(ising_batch_t *out, int32_t capacity, int64_t max_L, int6
 
 /*
  * Adds a packed lattice (L % 64 == 0, L <= max_L) that will run `sweeps`
- * sweeps at most (its history capacity).  tile_rows: rows per tile (4, 8, 16,
- * 32 or 64 dividing L, or 2 when L % 256 == 0; 0 = built-in choice).
+ * sweeps at most (its history capacity).  tile_rows: rows per tile (a power of
+ * two from 4 to 256 dividing L, or 2 when L % 256 == 0, whose shared-memory stage
+ * fits in 100 KB; 0 = built-in choice).
  * Writes the slot index to *idx.
  * Enqueues the start state.  Errors: EINVAL, ENOMEM (arena), EBUSY (slots).
  */
@@ -224,11 +225,11 @@ int ising_batch_synchronize(ising_batch_t b);
 int ising_batch_free(ising_batch_t b);
 
 /*
- * Times one half-sweep of a packed lattice of side L for each candidate
- * (tile_rows in {2,4,8,16,32,64} dividing L, 2 only when L % 256 == 0; threads in
- * {256, 512}) and returns
- * the fastest in *tile_rows, *threads and its time in *ms.  Uses its own
- * scratch lattice.  Errors: EINVAL, ENOMEM, ECUDA.
+ * Times sweeps of packed lattices of side L for each candidate (tile_rows a
+ * power of two from 2 to 256 accepted by ising_batch_add; threads 256 or 512),
+ * using enough copies of the lattice (up to 2^26 sites or 64) to give every SM
+ * work, and returns the fastest in *tile_rows, *threads and its time per sweep of
+ * one lattice in *ms.  Uses its own scratch batch.  Errors: EINVAL, ENOMEM, ECUDA.
  */
 int ising_autotune(int64_t L, int32_t *tile_rows, int32_t *threads, double *ms);
 

@@ -82,11 +82,17 @@ int64_t stage_bytes_for(int64_t L, int tile_rows)
     return (words * 4 + 15) / 16 * 16;
 }
 
-// Tile heights: 4..64 rows; 2 rows only when a row is a whole number of 16-byte
-// units (W % 4 == 0), so that every bulk copy stays 16-byte aligned.
+// Tile heights: powers of two from 4 to 256 rows; 2 rows only when a row is a
+// whole number of 16-byte units (W % 4 == 0), so that every bulk copy stays
+// 16-byte aligned.  The built-in choice stops at 64 rows: taller tiles pay only
+// when the tuner finds they do, since a batch of mid-size lattices cut into
+// 256-row tiles can hold fewer tiles than the persistent grid has CTAs.
+constexpr int kMaxTileRows = 256;
+constexpr int kDefaultMaxTileRows = 64;
+
 bool tile_rows_ok(int64_t L, int tr)
 {
-    const bool pow2 = tr == 2 || tr == 4 || tr == 8 || tr == 16 || tr == 32 || tr == 64;
+    const bool pow2 = tr >= 2 && tr <= kMaxTileRows && (tr & (tr - 1)) == 0;
     return pow2 && (tr >= 4 || (L / 64) % 4 == 0) && tr <= L && L % tr == 0 &&
            stage_bytes_for(L, tr) <= kStageCapBytes;
 }
@@ -98,10 +104,23 @@ bool tile_rows_ok(int64_t L, int tr)
 int default_tile_rows(int64_t L)
 {
     const int64_t W = L / 64;
-    int tr = 64;
+    int tr = kDefaultMaxTileRows;
     while (tr > 2 && ((int64_t)tr * W > ISING_TILE_WORDS || !tile_rows_ok(L, tr))) tr >>= 1;
     if (!tile_rows_ok(L, tr)) tr = 4;
     return tr;
+}
+
+// Tile height for a lattice swept on its own: as for a batch, but small lattices
+// are cut into enough tiles to spread over the persistent grid (about two CTAs
+// per SM) instead of a few large ones.
+int single_tile_rows(int64_t L)
+{
+    const int grid = 2 * sm_count();
+    int tr = 4;
+    while (tr < kMaxTileRows && L / tr > grid) tr *= 2;
+    tr = std::min(tr, default_tile_rows(L));
+    while (tr > 2 && !tile_rows_ok(L, tr)) tr >>= 1;
+    return tile_rows_ok(L, tr) ? tr : default_tile_rows(L);
 }
 
 // ---------------------------------------------------------------- engine
@@ -544,7 +563,7 @@ int ising_init_ex(ising_t* out, int64_t L, double beta, uint64_t seed, int start
         const int64_t plane_words = L * (L / 64);
         CKH(cudaMalloc(&h->planes, sizeof(uint32_t) * 2 * (size_t)plane_words));
         CKH(launch_packed_init(h->planes, h->planes + plane_words, L, seed, start, h->stream));
-        const int tr = default_tile_rows(L);
+        const int tr = single_tile_rows(L);
         LatticeDesc& d = h->desc;
         d.plane[0] = h->planes;
         d.plane[1] = h->planes + plane_words;
@@ -923,7 +942,7 @@ int ising_batch_create(ising_batch_t* out, int32_t capacity, int64_t max_L, int6
     // stage size: the largest tile any admissible lattice can use
     int64_t stage = 0;
     for (int64_t L = 64; L <= max_L; L += 64)
-        for (int tr = 2; tr <= 64; tr *= 2)
+        for (int tr = 2; tr <= kMaxTileRows; tr *= 2)
             if (tile_rows_ok(L, tr)) stage = std::max(stage, stage_bytes_for(L, tr));
     rc = b->eng.setup(capacity, (int)stage, threads, b->stream);
     if (!rc) rc = b->arena.init(arena_bytes);
@@ -1147,27 +1166,28 @@ int ising_autotune(int64_t L, int32_t* tile_rows, int32_t* threads, double* ms)
 {
     if (!tile_rows || !threads) return fail(ISING_EINVAL, "null output");
     if (L < 64 || L % 64 || L > kPackedMaxL) return fail(ISING_EINVAL, "L must be a multiple of 64");
+    // time as many copies of the lattice as it takes to give every SM work (up to
+    // 2^26 sites or 64 copies), as in a batch where this size is common
+    int copies = 1;
+    while (copies < 64 && (int64_t)copies * L * L < (1ll << 26)) copies *= 2;
+    const int reps = L >= 8192 ? 4 : 16;
     double best = 1e300;
     int best_tr = 0, best_th = 0;
     const int thread_opts[2] = {256, 512};
     for (int ti = 0; ti < 2; ++ti) {
         ising_batch_t b = nullptr;
-        const int64_t arena = (int64_t)sizeof(uint32_t) * 2 * L * (L / 64) + 16 * 64 + 4096;
-        int rc = ising_batch_create(&b, 1, L, arena, thread_opts[ti], nullptr);
+        const int64_t per = (int64_t)sizeof(uint32_t) * 2 * L * (L / 64) + 16 * (reps + 4) + 512;
+        int rc = ising_batch_create(&b, copies, L, per * copies + 4096, thread_opts[ti], nullptr);
         if (rc) return rc;
-        for (int tr = 2; tr <= 64; tr *= 2) {
+        for (int tr = 2; tr <= kMaxTileRows; tr *= 2) {
             if (!tile_rows_ok(L, tr)) continue;
-            int32_t idx = -1;
-            rc = ising_batch_add(b, L, 0.4406868, 12345, ISING_HOT, 64, tr, &idx);
-            if (rc) {
-                ising_batch_free(b);
-                return rc;
-            }
+            std::vector<int32_t> idx((size_t)copies, -1);
+            for (int k = 0; k < copies && !rc; ++k)
+                rc = ising_batch_add(b, L, 0.4406868, 12345 + k, ISING_HOT, reps + 4, tr, &idx[(size_t)k]);
             cudaEvent_t e0, e1;
             cudaEventCreate(&e0);
             cudaEventCreate(&e1);
-            rc = b->eng.run(2, 0);  // warm-up
-            const int reps = L >= 8192 ? 4 : 16;
+            if (!rc) rc = b->eng.run(2, 0);  // warm-up
             cudaEventRecord(e0, b->stream);
             if (!rc) rc = b->eng.run(reps, 0);
             cudaEventRecord(e1, b->stream);
@@ -1181,19 +1201,19 @@ int ising_autotune(int64_t L, int32_t* tile_rows, int32_t* threads, double* ms)
                 ising_batch_free(b);
                 return rc;
             }
-            const double per = (double)t / reps;
-            if (per < best) {
-                best = per;
+            const double per_sweep = (double)t / reps;
+            if (per_sweep < best) {
+                best = per_sweep;
                 best_tr = tr;
                 best_th = thread_opts[ti];
             }
-            ising_batch_remove(b, idx);
+            for (int k = 0; k < copies; ++k) ising_batch_remove(b, idx[(size_t)k]);
         }
         ising_batch_free(b);
     }
     *tile_rows = best_tr;
     *threads = best_th;
-    if (ms) *ms = best;
+    if (ms) *ms = best / copies;
     return ISING_OK;
 }
 

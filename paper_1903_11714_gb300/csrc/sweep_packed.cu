@@ -23,6 +23,7 @@
 // lands while the current one is computed.
 #include "ising_internal.cuh"
 #include "philox.cuh"
+#include "word_update.cuh"
 
 // Threads per SM the register allocation must leave room for (a CTA of NT
 // threads gets a register cap of 65536 / ISING_SWEEP_THREADS_PER_SM per thread).
@@ -168,40 +169,6 @@ __device__ __forceinline__ void issue_tile(const LatticeDesc& d, int local_tile,
     bulk_copy_g2s(s_src + (size_t)HB * W, src + (size_t)i0 * W, row_bytes * TR, bar);
     bulk_copy_g2s(s_src + (size_t)(HB + TR) * W, src + (size_t)ib * W, row_bytes * HB, bar);
     bulk_copy_g2s(s_tgt, tgt + (size_t)i0 * W, row_bytes * TR, bar);
-}
-
-// New value of one 32-site target word.
-__device__ __forceinline__ uint32_t update_word(uint32_t t, uint32_t up, uint32_t down, uint32_t same,
-                                                uint32_t hz, uint32_t q_lo, const PhiloxWordConsts& pc,
-                                                uint64_t key, uint32_t t2, uint32_t t4, uint32_t all2,
-                                                uint32_t all4)
-{
-    // anti-aligned neighbour bits and their 4-input sum n_anti = 4*b2 + 2*b1 + b0
-    const uint32_t au = t ^ up, ad = t ^ down, as = t ^ same, ah = t ^ hz;
-    const uint32_t s0 = au ^ ad, c0 = au & ad;
-    const uint32_t s1 = as ^ ah, c1 = as & ah;
-    const uint32_t b0 = s0 ^ s1, cc = s0 & s1;
-    const uint32_t b1 = c0 ^ c1 ^ cc;
-    const uint32_t b2 = c0 & c1;
-
-    uint32_t x[32];
-    philox_word8(q_lo, pc, key, x);
-    // Threshold tests as carry chains: sub.cc sets the carry flag iff x >= t (no
-    // borrow), and addc doubles the mask and adds that flag, so after 32 steps bit b
-    // of g holds [x[b] >= t]; two instructions per compare, no predicate-to-bit
-    // packing.  q = ~g is the mask of x < t.
-    uint32_t g2 = 0, g4 = 0;
-#pragma unroll
-    for (int b = 31; b >= 0; --b) {
-        asm("{\n\t.reg .u32 d;\n\tsub.cc.u32 d, %1, %2;\n\taddc.u32 %0, %0, %0;\n\t}" : "+r"(g2) : "r"(x[b]), "r"(t2));
-        asm("{\n\t.reg .u32 d;\n\tsub.cc.u32 d, %1, %2;\n\taddc.u32 %0, %0, %0;\n\t}" : "+r"(g4) : "r"(x[b]), "r"(t4));
-    }
-    const uint32_t q2 = all2 | ~g2;
-    const uint32_t q4 = all4 | ~g4;
-    // n_anti >= 2 (h <= 0): always; n_anti == 1 (h = 2): x < T2; n_anti == 0 (h = 4):
-    // x < T4.  T4 <= T2, so q4 is a subset of q2 and ORing q4 everywhere is exact.
-    const uint32_t flip = b1 | b2 | (b0 & q2) | q4;
-    return t ^ flip;
 }
 
 template <int NT, bool ONE>
@@ -457,80 +424,6 @@ __global__ void __launch_bounds__(NT, (ISING_SWEEP_THREADS_PER_SM / NT > 0 ? ISI
     if (colour == 1 && acc_lat >= 0) flush(acc_lat);
 }
 
-// Resident form for one small lattice: both planes live in this CTA's shared
-// memory for `nsweeps` sweeps, with a block barrier between half-sweeps instead
-// of a kernel launch.  Same words, neighbours, draws and decisions as the tiled
-// kernel; the white pass writes (M, E) of each sweep straight into the history.
-template <int NT>
-__global__ void __launch_bounds__(NT, 1) packed_resident_kernel(const __grid_constant__ LatticeDesc d, int nsweeps)
-{
-    extern __shared__ __align__(16) uint32_t planes_s[];
-    __shared__ uint32_t red[2 * (NT / 32)];
-    const int W = d.W, L = d.L;
-    const int words = L * W;
-    uint32_t* pl[2] = {planes_s, planes_s + words};
-    const int tid = threadIdx.x;
-    for (int k = tid; k < words; k += NT) {
-        pl[0][k] = d.plane[0][k];
-        pl[1][k] = d.plane[1][k];
-    }
-    __syncthreads();
-    const uint64_t key = d.key;
-    const bool q_small = L <= 131072;
-    for (int s = 0; s < nsweeps; ++s) {
-        const uint32_t sweep = d.sweep + (uint32_t)s;
-        for (int colour = 0; colour < 2; ++colour) {
-            const uint32_t* src = pl[colour ^ 1];
-            uint32_t* tgt = pl[colour];
-            const PhiloxWordConsts pc_all = philox_consts(key, 0u, sweep, (uint32_t)colour);
-            uint32_t ups = 0, anti = 0;
-            for (int idx = tid; idx < words; idx += NT) {
-                const int i = idx / W, w = idx - i * W;
-                const int iu = i == 0 ? L - 1 : i - 1, id = i + 1 == L ? 0 : i + 1;
-                const uint32_t up = src[iu * W + w], down = src[id * W + w], same = src[idx];
-                uint32_t hz;
-                if ((i + colour) & 1)
-                    hz = __funnelshift_r(same, src[i * W + (w + 1 == W ? 0 : w + 1)], 1);
-                else
-                    hz = __funnelshift_l(src[i * W + (w == 0 ? W - 1 : w - 1)], same, 1);
-                const uint64_t q0 = (uint64_t)i * (uint64_t)(L >> 3) + 8ull * (uint64_t)w;
-                const PhiloxWordConsts pc =
-                    q_small ? pc_all : philox_consts(key, (uint32_t)(q0 >> 32), sweep, (uint32_t)colour);
-                const uint32_t nw =
-                    update_word(tgt[idx], up, down, same, hz, (uint32_t)q0, pc, key, d.t2, d.t4, d.all2, d.all4);
-                tgt[idx] = nw;
-                if (colour == 1) {
-                    ups += __popc(nw) + __popc(same);
-                    anti += __popc(nw ^ up) + __popc(nw ^ down) + __popc(nw ^ same) + __popc(nw ^ hz);
-                }
-            }
-            if (colour == 1) {
-                const uint32_t u = __reduce_add_sync(0xffffffffu, ups);
-                const uint32_t a = __reduce_add_sync(0xffffffffu, anti);
-                if ((tid & 31) == 0) {
-                    red[2 * (tid >> 5)] = u;
-                    red[2 * (tid >> 5) + 1] = a;
-                }
-            }
-            __syncthreads();
-            if (colour == 1 && tid == 0) {
-                int64_t su = 0, sa = 0;
-                for (int k = 0; k < NT / 32; ++k) {
-                    su += red[2 * k];
-                    sa += red[2 * k + 1];
-                }
-                const int64_t N = (int64_t)L * L;
-                d.hist[2 * (int64_t)sweep] = 2 * su - N;
-                d.hist[2 * (int64_t)sweep + 1] = 2 * sa - 2 * N;
-            }
-        }
-    }
-    for (int k = tid; k < words; k += NT) {
-        d.plane[0][k] = pl[0][k];
-        d.plane[1][k] = pl[1][k];
-    }
-}
-
 // After `steps` sweeps: advance each live lattice's sweep counter (bounded by its target).
 __global__ void packed_advance_kernel(LatticeDesc* desc, const int32_t* count, int steps)
 {
@@ -623,22 +516,6 @@ cudaError_t packed_occupancy(int threads, size_t smem, int* blocks_per_sm)
     default:
         return cudaErrorInvalidValue;
     }
-}
-
-int packed_resident_max_L() { return 256; }
-
-cudaError_t launch_packed_resident(const LatticeDesc& d, int nsweeps, cudaStream_t s)
-{
-    const size_t smem = sizeof(uint32_t) * 2 * (size_t)d.L * (size_t)d.W;
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(packed_resident_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)(sizeof(uint32_t) * 2 * 256 * 4));
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
-    packed_resident_kernel<256><<<1, 256, smem, s>>>(d, nsweeps);
-    return cudaGetLastError();
 }
 
 cudaError_t launch_packed_advance(LatticeDesc* desc, const int32_t* count, int max_count, int steps, cudaStream_t s)

@@ -1,0 +1,97 @@
+// Resident sweep of one small bit-packed lattice: both colour planes stay in one
+// CTA's shared memory for many sweeps, with a block barrier between half-sweeps
+// instead of a kernel launch (the checkerboard schedule of Sec. 3.1).
+#include "ising_internal.cuh"
+#include "philox.cuh"
+#include "word_update.cuh"
+
+namespace ising {
+namespace {
+
+// Resident form for one small lattice: both planes live in this CTA's shared
+// memory for `nsweeps` sweeps, with a block barrier between half-sweeps instead
+// of a kernel launch.  Same words, neighbours, draws and decisions as the tiled
+// kernel; the white pass writes (M, E) of each sweep straight into the history.
+template <int NT>
+__global__ void __launch_bounds__(NT, 1) packed_resident_kernel(const __grid_constant__ LatticeDesc d, int nsweeps)
+{
+    extern __shared__ __align__(16) uint32_t planes_s[];
+    __shared__ uint32_t red[2 * (NT / 32)];
+    const int W = d.W, L = d.L;
+    const int words = L * W;
+    uint32_t* pl[2] = {planes_s, planes_s + words};
+    const int tid = threadIdx.x;
+    for (int k = tid; k < words; k += NT) {
+        pl[0][k] = d.plane[0][k];
+        pl[1][k] = d.plane[1][k];
+    }
+    __syncthreads();
+    const uint64_t key = d.key;
+    const bool q_small = L <= 131072;
+    for (int s = 0; s < nsweeps; ++s) {
+        const uint32_t sweep = d.sweep + (uint32_t)s;
+        for (int colour = 0; colour < 2; ++colour) {
+            const uint32_t* src = pl[colour ^ 1];
+            uint32_t* tgt = pl[colour];
+            const PhiloxWordConsts pc_all = philox_consts(key, 0u, sweep, (uint32_t)colour);
+            uint32_t ups = 0, anti = 0;
+            for (int idx = tid; idx < words; idx += NT) {
+                const int i = idx / W, w = idx - i * W;
+                const int iu = i == 0 ? L - 1 : i - 1, id = i + 1 == L ? 0 : i + 1;
+                const uint32_t up = src[iu * W + w], down = src[id * W + w], same = src[idx];
+                uint32_t hz;
+                if ((i + colour) & 1)
+                    hz = __funnelshift_r(same, src[i * W + (w + 1 == W ? 0 : w + 1)], 1);
+                else
+                    hz = __funnelshift_l(src[i * W + (w == 0 ? W - 1 : w - 1)], same, 1);
+                const uint64_t q0 = (uint64_t)i * (uint64_t)(L >> 3) + 8ull * (uint64_t)w;
+                const PhiloxWordConsts pc =
+                    q_small ? pc_all : philox_consts(key, (uint32_t)(q0 >> 32), sweep, (uint32_t)colour);
+                const uint32_t nw =
+                    update_word(tgt[idx], up, down, same, hz, (uint32_t)q0, pc, key, d.t2, d.t4, d.all2, d.all4);
+                tgt[idx] = nw;
+                if (colour == 1) {
+                    ups += __popc(nw) + __popc(same);
+                    anti += __popc(nw ^ up) + __popc(nw ^ down) + __popc(nw ^ same) + __popc(nw ^ hz);
+                }
+            }
+            if (colour == 1) {
+                const uint32_t u = __reduce_add_sync(0xffffffffu, ups);
+                const uint32_t a = __reduce_add_sync(0xffffffffu, anti);
+                if ((tid & 31) == 0) {
+                    red[2 * (tid >> 5)] = u;
+                    red[2 * (tid >> 5) + 1] = a;
+                }
+            }
+            __syncthreads();
+            if (colour == 1 && tid == 0) {
+                int64_t su = 0, sa = 0;
+                for (int k = 0; k < NT / 32; ++k) {
+                    su += red[2 * k];
+                    sa += red[2 * k + 1];
+                }
+                const int64_t N = (int64_t)L * L;
+                d.hist[2 * (int64_t)sweep] = 2 * su - N;
+                d.hist[2 * (int64_t)sweep + 1] = 2 * sa - 2 * N;
+            }
+        }
+    }
+    for (int k = tid; k < words; k += NT) {
+        d.plane[0][k] = pl[0][k];
+        d.plane[1][k] = pl[1][k];
+    }
+}
+
+}  // namespace
+
+int packed_resident_max_L() { return 256; }
+
+cudaError_t launch_packed_resident(const LatticeDesc& d, int nsweeps, cudaStream_t s)
+{
+    // both planes: 2 * L * L/64 words, at most 8 KB for L <= 256 (within the default limit)
+    const size_t smem = sizeof(uint32_t) * 2 * (size_t)d.L * (size_t)d.W;
+    packed_resident_kernel<256><<<1, 256, smem, s>>>(d, nsweeps);
+    return cudaGetLastError();
+}
+
+}  // namespace ising

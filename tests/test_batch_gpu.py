@@ -111,7 +111,7 @@ def test_uneven_batch_full_size():
     b.close()
 
 
-@pytest.mark.parametrize("tile_rows", [4, 8, 16, 32, 64])
+@pytest.mark.parametrize("tile_rows", [2, 4, 8, 16, 32, 64, 128, 256])
 def test_tile_rows_do_not_change_the_chain(tile_rows):
     L, beta, seed = 512, 0.44, 9
     ref, Mr, Er, _ = oracle.run(L, beta, seed, oracle.HOT, 6)
@@ -190,4 +190,4 @@ def test_admission_errors():
 def test_autotune_returns_a_valid_tile():
     for L in (64, 1024, 4096):
         tr, th, ms = ising.ising_autotune(L)
-        assert tr in (4, 8, 16, 32, 64) and L % tr == 0 and th in (256, 512) and ms > 0
+        assert tr in (2, 4, 8, 16, 32, 64, 128, 256) and L % tr == 0 and th in (256, 512) and ms > 0
