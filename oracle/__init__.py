@@ -5,7 +5,9 @@ CPU-baseline leg of ``bench.py`` may import this package.  The library path
 never imports it, and it shares no code with the CUDA path.
 
 The chain itself lives in ``ising_oracle.c`` (plain C, one site at a time, its
-own Philox4x32-10); this module builds it with gcc and wraps it with ctypes.
+own Philox4x32-10) and, for the three-dimensional generalisation the paper's
+conclusion names, ``ising3d_oracle.c``; this module builds both with gcc into one
+shared object and wraps them with ctypes.
 ``exact.py`` holds the closed forms and exact enumerations the oracle is pinned
 against.
 
@@ -31,7 +33,7 @@ import numpy as np
 os.environ.setdefault("OMP_WAIT_POLICY", "PASSIVE")
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = os.path.join(_HERE, "ising_oracle.c")
+_SRCS = [os.path.join(_HERE, "ising_oracle.c"), os.path.join(_HERE, "ising3d_oracle.c")]
 _LIB_PATH = os.path.join(_HERE, "_ising_oracle.so")
 _lib = None
 _lock = threading.Lock()
@@ -42,10 +44,11 @@ INIT_SWEEP = 0xFFFFFFFF  # counter word 2 reserved for the hot start
 
 def build(force: bool = False) -> str:
     """Compile ising_oracle.c into a shared object next to it (gcc, OpenMP)."""
-    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+    newest = max(os.path.getmtime(p) for p in _SRCS)
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < newest:
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
         subprocess.check_call(
-            ["gcc", "-O2", "-fopenmp", "-shared", "-fPIC", "-std=c11", "-o", tmp, _SRC, "-lm"]
+            ["gcc", "-O2", "-fopenmp", "-shared", "-fPIC", "-std=c11", "-o", tmp, *_SRCS, "-lm"]
         )
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -90,6 +93,23 @@ def lib():
             L.oracle_half_sweep_rows.argtypes = [i8p, ctypes.c_int64, ctypes.c_int, ctypes.c_double,
                                                  ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int64, ctypes.c_int64]
             L.oracle_half_sweep_rows.restype = ctypes.c_int64
+            dims = [ctypes.c_int64, ctypes.c_int64, ctypes.c_int64]
+            L.oracle3d_thresholds.argtypes = [ctypes.c_double, u64p]
+            L.oracle3d_thresholds.restype = None
+            L.oracle3d_accept.argtypes = [ctypes.c_int, ctypes.c_uint32, u64p]
+            L.oracle3d_accept.restype = ctypes.c_int
+            L.oracle3d_site_word.argtypes = dims + [ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
+                                                    ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int]
+            L.oracle3d_site_word.restype = ctypes.c_uint32
+            L.oracle3d_init.argtypes = [i8p] + dims + [ctypes.c_uint64, ctypes.c_int]
+            L.oracle3d_init.restype = None
+            L.oracle3d_observe.argtypes = [i8p] + dims + [i64p, i64p]
+            L.oracle3d_observe.restype = None
+            L.oracle3d_half_sweep_words.argtypes = [i8p] + dims + [ctypes.c_int, u64p, u32p]
+            L.oracle3d_half_sweep_words.restype = ctypes.c_int64
+            L.oracle3d_run.argtypes = [i8p] + dims + [ctypes.c_double, ctypes.c_uint64, ctypes.c_int64,
+                                                      ctypes.c_int64, i64p, i64p, ctypes.c_int]
+            L.oracle3d_run.restype = ctypes.c_int64
             _lib = L
     return _lib
 
@@ -218,6 +238,75 @@ def moments_exact(M, E, N: int, burn_in: int) -> dict:
     return {"n": n, "S1": S1, "S2": S2, "S4": S4, "SE": SE, "SE2": SE2,
             "abs_m": float(m1), "m2": float(m2), "m4": float(m4), "e": float(e1), "e2": float(e2),
             "binder": float(binder)}
+
+
+# ------------------------------------------------- three-dimensional torus
+# The Sec. 3 Hamiltonian on the cubic lattice (d = 3) with the same checkerboard
+# rules; see the header of ising3d_oracle.c.  Lattices are int8 arrays of shape
+# (X, Y, Z), all extents even; the library's lattices are cubic, X = Y = Z = L.
+
+def thresholds3d(beta: float) -> tuple[int, int, int]:
+    """(T_2, T_4, T_6): min(2^32, ceil(exp(-2 beta h) 2^32)) for h = 2, 4, 6."""
+    T = np.zeros(3, dtype=np.uint64)
+    lib().oracle3d_thresholds(float(beta), _ptr(T, ctypes.c_uint64))
+    return int(T[0]), int(T[1]), int(T[2])
+
+
+def accept3d(h: int, x: int, T) -> bool:
+    t = np.asarray(T, dtype=np.uint64)
+    return bool(lib().oracle3d_accept(int(h), int(x), _ptr(t, ctypes.c_uint64)))
+
+
+def site_word3d(dims, i: int, j: int, k: int, seed: int, sweep: int, c: int) -> int:
+    X, Y, Z = dims
+    return int(lib().oracle3d_site_word(X, Y, Z, i, j, k, seed, sweep, c))
+
+
+def _check_dims(dims) -> tuple[int, int, int]:
+    X, Y, Z = (int(v) for v in dims)
+    if min(X, Y, Z) < 2 or X % 2 or Y % 2 or Z % 2:
+        raise ValueError("the 3D oracle takes even extents >= 2")
+    return X, Y, Z
+
+
+def init3d(dims, seed: int, start: int = HOT) -> np.ndarray:
+    X, Y, Z = _check_dims(dims)
+    s = np.empty((X, Y, Z), dtype=np.int8)
+    lib().oracle3d_init(_ptr(s, ctypes.c_int8), X, Y, Z, int(seed), int(start))
+    return s
+
+
+def observe3d(s: np.ndarray) -> tuple[int, int]:
+    """(M, E) with M = sum sigma and E = H(sigma) over the 3N bonds."""
+    s = np.ascontiguousarray(s, dtype=np.int8)
+    X, Y, Z = _check_dims(s.shape)
+    M = ctypes.c_int64()
+    E = ctypes.c_int64()
+    lib().oracle3d_observe(_ptr(s, ctypes.c_int8), X, Y, Z, ctypes.byref(M), ctypes.byref(E))
+    return M.value, E.value
+
+
+def half_sweep_words3d(s: np.ndarray, c: int, T, words: np.ndarray) -> int:
+    """One colour-c half-sweep with caller-given uniform words; returns sum of 2h."""
+    assert s.flags.c_contiguous and s.dtype == np.int8
+    X, Y, Z = _check_dims(s.shape)
+    w = np.ascontiguousarray(words, dtype=np.uint32)
+    assert w.shape == s.shape
+    t = np.asarray(T, dtype=np.uint64)
+    return int(lib().oracle3d_half_sweep_words(_ptr(s, ctypes.c_int8), X, Y, Z, int(c), _ptr(t, ctypes.c_uint64),
+                                               _ptr(w, ctypes.c_uint32)))
+
+
+def run3d(dims, beta: float, seed: int, start: int = HOT, sweeps: int = 1, sweep0: int = 0,
+          state: np.ndarray | None = None, check: bool = False):
+    """3D checkerboard chain: returns (final state, M[sweeps], E[sweeps], mismatches)."""
+    X, Y, Z = _check_dims(dims)
+    s = init3d((X, Y, Z), seed, start) if state is None else np.ascontiguousarray(state, dtype=np.int8).copy()
+    M = np.zeros(sweeps, dtype=np.int64)
+    E = np.zeros(sweeps, dtype=np.int64)
+    mism = lib().oracle3d_run(_ptr(s, ctypes.c_int8), X, Y, Z, float(beta), int(seed), int(sweep0), int(sweeps),
+                              _ptr(M, ctypes.c_int64), _ptr(E, ctypes.c_int64), 1 if check else 0)
+    return s, M, E, int(mism)
 
 
 def _check_L(L: int) -> None:

@@ -13,6 +13,9 @@ independent anchors the Monte Carlo oracle is pinned against:
   finite-torus partition function; the energy is -d ln Z / d beta.
 * ``onsager_m0`` -- Onsager/Yang spontaneous magnetisation (1 - sinh^-4(2 beta))^(1/8)
   for beta > beta_c, beta_c = ln(1 + sqrt 2)/2 (Sec. 4.1).
+* ``enumerate3d_observables`` / ``stationarity_residual3d`` -- the same brute
+  force and exact pi P_c = pi check on a small X x Y x Z torus (the Sec. 3
+  Hamiltonian with d = 3), for the three-dimensional generalisation.
 """
 from __future__ import annotations
 
@@ -191,3 +194,69 @@ def binned_error(x, nbins: int = 32) -> tuple[float, float]:
     n = (len(x) // nbins) * nbins
     b = x[len(x) - n:].reshape(nbins, -1).mean(axis=1)
     return float(x[len(x) - n:].mean()), float(b.std(ddof=1) / math.sqrt(nbins))
+
+
+# ------------------------------------------------- three-dimensional torus
+def _all_states3d(dims) -> np.ndarray:
+    X, Y, Z = dims
+    N = X * Y * Z
+    if N > 20:
+        raise ValueError("enumeration is for X*Y*Z <= 20")
+    idx = np.arange(1 << N, dtype=np.uint32)
+    bits = (idx[:, None] >> np.arange(N, dtype=np.uint32)) & 1
+    return (1 - 2 * bits.astype(np.int8)).reshape(-1, X, Y, Z)
+
+
+def _energies3d(s: np.ndarray) -> np.ndarray:
+    """H = -sum over the bonds (s, s + e_a), a = x, y, z, of every state in s."""
+    s = s.astype(np.int64)
+    return -sum((s * np.roll(s, -1, axis=a)).sum(axis=(1, 2, 3)) for a in (1, 2, 3))
+
+
+def enumerate3d_observables(dims, beta: float) -> dict:
+    """<E>/N, <|M|>/N, <m^2>, <m^4>, U4 on the X x Y x Z torus by summing over every state."""
+    s = _all_states3d(dims)
+    N = int(np.prod(dims))
+    E = _energies3d(s).astype(np.float64)
+    M = s.astype(np.int64).sum(axis=(1, 2, 3)).astype(np.float64)
+    w = np.exp(-beta * (E - E.min()))
+    Z = w.sum()
+    m2 = (w * (M / N) ** 2).sum() / Z
+    m4 = (w * (M / N) ** 4).sum() / Z
+    return {"e": (w * E).sum() / Z / N, "abs_m": (w * np.abs(M)).sum() / Z / N, "m2": m2, "m4": m4,
+            "binder": 1.0 - m4 / (3.0 * m2 * m2)}
+
+
+def stationarity_residual3d(dims, beta: float, colour: int, flip_prob) -> float:
+    """max |pi P_c - pi| / max pi for one colour-c half-sweep on the X x Y x Z torus.
+
+    P_c flips each site of colour (i+j+k) mod 2 = c independently with probability
+    flip_prob(h), h = sigma * (sum of the six neighbours), the other colour fixed.
+    """
+    X, Y, Z = dims
+    s = _all_states3d(dims)
+    E = _energies3d(s).astype(np.float64)
+    pi = np.exp(-beta * (E - E.min()))
+    pi /= pi.sum()
+    sites = [(i, j, k) for i in range(X) for j in range(Y) for k in range(Z) if (i + j + k) % 2 == colour]
+    f = np.empty((s.shape[0], len(sites)))
+    for n, (i, j, k) in enumerate(sites):
+        nn = (s[:, (i - 1) % X, j, k].astype(np.int64) + s[:, (i + 1) % X, j, k]
+              + s[:, i, (j - 1) % Y, k] + s[:, i, (j + 1) % Y, k]
+              + s[:, i, j, (k - 1) % Z] + s[:, i, j, (k + 1) % Z])
+        h = s[:, i, j, k].astype(np.int64) * nn
+        f[:, n] = np.vectorize(flip_prob, otypes=[np.float64])(h)
+    bitpos = np.array([(i * Y + j) * Z + k for i, j, k in sites], dtype=np.uint32)
+    state_idx = np.arange(s.shape[0], dtype=np.uint32)
+    out = np.zeros_like(pi)
+    for F in range(1 << len(sites)):
+        prob = pi.copy()
+        mask = np.uint32(0)
+        for n in range(len(sites)):
+            if (F >> n) & 1:
+                prob *= f[:, n]
+                mask |= np.uint32(1) << bitpos[n]
+            else:
+                prob *= 1.0 - f[:, n]
+        np.add.at(out, state_idx ^ mask, prob)
+    return float(np.abs(out - pi).max() / pi.max())

@@ -1,0 +1,182 @@
+/*
+ * ising3d_oracle.c -- plain CPU oracle for the checkerboard Metropolis sweep of the
+ * 3D nearest-neighbour Ising model on an X x Y x Z torus.
+ *
+ * TEST INFRASTRUCTURE ONLY, like ising_oracle.c (built into the same shared
+ * object): only the tests, the package smoke check and the benchmark's CPU
+ * baseline leg use it, and it shares no code, header or table with the CUDA path.
+ *
+ * What it computes: the Hamiltonian of Sec. 3 on the d-dimensional hypercubic
+ * lattice, here d = 3, mu = 0, J = 1: H = -sum over nearest-neighbour pairs of
+ * sigma_i sigma_j on the torus, i.e. the 3N bonds (s, s + e_x), (s, s + e_y),
+ * (s, s + e_z).  The paper states that its checkerboard algorithm generalises to
+ * three dimensions (Conclusion); the generalisation used here keeps every rule of
+ * the 2D chain (Sec. 3.1 and Algorithms 1-2) and changes only the neighbourhood:
+ *   - colour c(i,j,k) = (i+j+k) mod 2, black (0) then white (1) in every sweep;
+ *     all six neighbours of a site have the other colour, so one half-sweep
+ *     updates a colour with the other fixed (the factorised kernel of Sec. 3.1);
+ *   - nn = sum of the six neighbours, h = sigma * nn in {-6, ..., 6}; the site
+ *     flips with probability min{1, exp(-2 beta h)}: always for h <= 0, else iff
+ *     the uniform word x is below T_h = min(2^32, ceil(exp(-2 beta h) 2^32)),
+ *     h = 2, 4, 6, evaluated in FP64 by the host libm.
+ *
+ * Readings (the paper gives no 3D algorithm; these mirror the 2D readings):
+ *   - Site (i,j,k) has colour-plane index p = (i*Y + j)*(Z/2) + (k>>1): the 2D
+ *     index with the row (i,j) numbered i*Y + j.  Its uniform is output word
+ *     (p & 3) of Philox4x32-10 with key (seed low, seed high) and counter
+ *     (sweep, q low 32, c, q high 32), q = p >> 2 -- the 2D layout.
+ *   - Hot start: sigma = +1 iff the word drawn with sweep = 0xFFFFFFFF is below
+ *     2^31; cold start all +1.
+ *   - M = sum sigma; E = H = -sum over the 3N bonds.  A dimension of extent 2
+ *     makes the two neighbours along it the same site, counted twice in nn and
+ *     bonded twice in H, so the chain stays the Metropolis chain of that H.
+ *   - All extents are even (so that the colouring is consistent on the torus).
+ *
+ * Pins (tests/test_oracle_3d.py): thresholds against 50-digit arithmetic; the
+ * chain against exact enumeration on the 2x2x4 torus; exact stationarity of the
+ * quantised half-sweep kernel; deterministic limits (beta = 0, zero temperature)
+ * against a separately written numpy rule; the incremental-energy invariant.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+
+#define ORACLE_API __attribute__((visibility("default")))
+
+/* Philox4x32-10 of ising_oracle.c (same shared object). */
+void oracle_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+
+static inline int64_t wrap3(int64_t a, int64_t n)
+{
+    a %= n;
+    return a < 0 ? a + n : a;
+}
+
+/* Thresholds for h = 2, 4, 6: T[n] = min(2^32, ceil(exp(-2 beta h) 2^32)), h = 2(n+1). */
+ORACLE_API void oracle3d_thresholds(double beta, uint64_t T[3])
+{
+    for (int n = 0; n < 3; ++n) {
+        int h = 2 * (n + 1);
+        double t = ceil(exp(-2.0 * beta * (double)h) * 4294967296.0);
+        if (t > 4294967296.0) t = 4294967296.0;
+        if (t < 0.0) t = 0.0;
+        T[n] = (uint64_t)t;
+    }
+}
+
+/* Metropolis decision of one site: flip iff h <= 0, or x below the threshold of h. */
+ORACLE_API int oracle3d_accept(int h, uint32_t x, const uint64_t T[3])
+{
+    if (h <= 0) return 1;
+    return (uint64_t)x < T[h / 2 - 1];
+}
+
+ORACLE_API uint32_t oracle3d_site_word(int64_t X, int64_t Y, int64_t Z, int64_t i, int64_t j, int64_t k,
+                                       uint64_t seed, uint32_t sweep, int c)
+{
+    (void)X;
+    uint64_t p = ((uint64_t)i * (uint64_t)Y + (uint64_t)j) * (uint64_t)(Z / 2) + (uint64_t)(k >> 1);
+    uint64_t q = p >> 2;
+    uint32_t ctr[4] = {sweep, (uint32_t)q, (uint32_t)c, (uint32_t)(q >> 32)};
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t out[4];
+    oracle_philox4x32_10(ctr, key, out);
+    return out[p & 3];
+}
+
+#define AT(s, i, j, k) (s)[((i) * Y + (j)) * Z + (k)]
+
+/* start: 0 = hot, 1 = cold. */
+ORACLE_API void oracle3d_init(int8_t *s, int64_t X, int64_t Y, int64_t Z, uint64_t seed, int start)
+{
+#pragma omp parallel for schedule(static) if (X * Y * Z >= 32768)
+    for (int64_t i = 0; i < X; ++i)
+        for (int64_t j = 0; j < Y; ++j)
+            for (int64_t k = 0; k < Z; ++k) {
+                if (start == 1) {
+                    AT(s, i, j, k) = 1;
+                } else {
+                    uint32_t x = oracle3d_site_word(X, Y, Z, i, j, k, seed, 0xFFFFFFFFu, (int)((i + j + k) & 1));
+                    AT(s, i, j, k) = (x < 0x80000000u) ? 1 : -1;
+                }
+            }
+}
+
+/* M = sum sigma, E = -sum over the 3N torus bonds. */
+ORACLE_API void oracle3d_observe(const int8_t *s, int64_t X, int64_t Y, int64_t Z, int64_t *M, int64_t *E)
+{
+    int64_t m = 0, e = 0;
+#pragma omp parallel for reduction(+ : m, e) schedule(static) if (X * Y * Z >= 32768)
+    for (int64_t i = 0; i < X; ++i)
+        for (int64_t j = 0; j < Y; ++j)
+            for (int64_t k = 0; k < Z; ++k) {
+                int64_t v = AT(s, i, j, k);
+                m += v;
+                e -= v * (AT(s, wrap3(i + 1, X), j, k) + AT(s, i, wrap3(j + 1, Y), k) + AT(s, i, j, wrap3(k + 1, Z)));
+            }
+    *M = m;
+    *E = e;
+}
+
+/* One half-sweep of colour c.  words == NULL draws from Philox; otherwise
+ * words[(i*Y + j)*Z + k] is the uniform word of site (i,j,k) (a test hook).
+ * Returns the energy change, the sum of 2h over accepted flips. */
+static int64_t half_sweep3d(int8_t *s, int64_t X, int64_t Y, int64_t Z, int c, const uint64_t T[3],
+                            uint64_t seed, uint32_t sweep, const uint32_t *words)
+{
+    int64_t dE = 0;
+#pragma omp parallel for reduction(+ : dE) schedule(static) if (X * Y * Z >= 32768)
+    for (int64_t i = 0; i < X; ++i)
+        for (int64_t j = 0; j < Y; ++j)
+            for (int64_t k = 0; k < Z; ++k) {
+                if (((i + j + k) & 1) != c) continue;
+                int nn = AT(s, wrap3(i - 1, X), j, k) + AT(s, wrap3(i + 1, X), j, k)
+                       + AT(s, i, wrap3(j - 1, Y), k) + AT(s, i, wrap3(j + 1, Y), k)
+                       + AT(s, i, j, wrap3(k - 1, Z)) + AT(s, i, j, wrap3(k + 1, Z));
+                int h = AT(s, i, j, k) * nn;
+                uint32_t x = words ? words[(i * Y + j) * Z + k]
+                                   : oracle3d_site_word(X, Y, Z, i, j, k, seed, sweep, c);
+                if (oracle3d_accept(h, x, T)) {
+                    AT(s, i, j, k) = (int8_t)(-AT(s, i, j, k));
+                    dE += 2 * h;
+                }
+            }
+    return dE;
+}
+
+ORACLE_API int64_t oracle3d_half_sweep_words(int8_t *s, int64_t X, int64_t Y, int64_t Z, int c,
+                                             const uint64_t T[3], const uint32_t *words)
+{
+    return half_sweep3d(s, X, Y, Z, c, T, 0, 0, words);
+}
+
+/* Sweeps sweep0 .. sweep0+nsweeps-1 (black then white) on s; M[k], E[k] after
+ * each sweep when non-NULL.  check != 0 also carries E incrementally and compares
+ * it with the recomputed value after every half-sweep; returns the mismatches. */
+ORACLE_API int64_t oracle3d_run(int8_t *s, int64_t X, int64_t Y, int64_t Z, double beta, uint64_t seed,
+                                int64_t sweep0, int64_t nsweeps, int64_t *M, int64_t *E, int check)
+{
+    uint64_t T[3];
+    oracle3d_thresholds(beta, T);
+    int64_t mism = 0, m0 = 0, e_inc = 0;
+    if (check) oracle3d_observe(s, X, Y, Z, &m0, &e_inc);
+    for (int64_t n = 0; n < nsweeps; ++n) {
+        uint32_t sweep = (uint32_t)(sweep0 + n);
+        for (int c = 0; c < 2; ++c) {
+            int64_t dE = half_sweep3d(s, X, Y, Z, c, T, seed, sweep, NULL);
+            if (check) {
+                int64_t m, e;
+                e_inc += dE;
+                oracle3d_observe(s, X, Y, Z, &m, &e);
+                if (e != e_inc) ++mism;
+            }
+        }
+        if (M || E) {
+            int64_t m, e;
+            oracle3d_observe(s, X, Y, Z, &m, &e);
+            if (M) M[n] = m;
+            if (E) E[n] = e;
+        }
+    }
+    return mism;
+}
