@@ -32,13 +32,14 @@ sys.path.insert(0, ROOT)
 METRIC = "spin-flip attempts/ns on 1 GB300 (bit-packed checkerboard sweep, bit-exact)"
 UNIT = "flips/ns"
 # Algorithmic work per site update.  A Philox4x32-10 call serves 4 sites with 10
-# rounds of two 32x32->64 products and two three-input XORs; the round-1 and
-# round-2 products (and one XOR) that do not depend on the site are formed once per
-# 32-site word, leaving 18 products + 19 XORs per call: 4.5 products and 4.75 XORs
-# per site.  The acceptance test adds 2 threshold compares per site and the
-# neighbour count / flip mask ~12 bitwise operations per 32 sites.
-MULS_PER_SITE_SWEEP = 4.5
-ALU_OPS_PER_SITE = 4.75 + 2.0 + 0.375
+# rounds of two 32x32->64 products and two three-input XORs.  The site index enters
+# through counter word 1, so the two round-1 products, round 2's B product and
+# round 3's A product do not depend on the site and are formed once per launch,
+# leaving 16 products + 18 XORs per call: 4 products and 4.5 XORs per site.  The
+# acceptance test adds 2 threshold compares per site and the neighbour count /
+# flip mask ~12 bitwise operations per 32 sites.
+MULS_PER_SITE_SWEEP = 4.0
+ALU_OPS_PER_SITE = 4.5 + 2.0 + 0.375
 # Integer multiply pipe: 16 lanes per scheduler, 4 schedulers per SM, a 32x32->64
 # product taking two lane-cycles -> 32 products per clock per SM.  Logic and
 # compare instructions run on the ALU pipe: 64 per clock per SM.
@@ -316,6 +317,120 @@ def run_batched(args, which: str) -> None:
                       "note": f"plain = each lattice alone with its own launches, {n_plain} sweeps each"}))
 
 
+def run_cubic(args) -> None:
+    """3D checkerboard sweep (the paper's d-dimensional Hamiltonian at d = 3, Sec. 3 and
+    Conclusion): one L = 2048 lattice at beta_c of the cubic lattice, CUDA events over
+    the timed sweeps on the handle's stream; roofline on the same multiply-pipe peak."""
+    import torch
+
+    from paper_1903_11714_gb300 import ising, workloads
+
+    cfg = workloads.cubic_large()
+    L = args.L or cfg.L
+    N = L ** 3
+    steps = args.steps if args.steps != 200 else cfg.sweeps
+    st = torch.cuda.Stream()
+    lat = ising.Lattice3D(L, cfg.beta, cfg.seed, cfg.start, stream=st)
+    lat.sweep(args.warmup)
+    lat.synchronize()
+    peaks = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    time.sleep(0.3)
+    e0, e1 = _events(torch, st)
+    torch.cuda.synchronize()
+    e0.record(st)
+    lat.sweep(steps)
+    e1.record(st)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    lat.synchronize()
+    ms = e0.elapsed_time(e1)
+    lat.close()
+    value = steps * N / (ms * 1e6)
+    t_launch_s = ms * 1e-3 / (2 * steps)
+    achieved = MULS_PER_SITE_SWEEP * N / 2 / t_launch_s / 1e12
+    peak = MULS_PER_CLK_SM * N_SMS * sm_max * 1e6 / 1e12
+    alu_ops = 4.5 + 3.0 + 0.6  # Philox XORs, three threshold compares, 6-input adder and flip
+    cpu = None
+    if not args.no_cpu_baseline:
+        cpu = cubic_cpu_baseline(cfg.beta, cfg.seed)
+    print(json.dumps({
+        "metric": "spin-flip attempts/ns, 3D cubic lattice (bit-packed checkerboard sweep, bit-exact)",
+        "workload": "cubic", "unit": UNIT, "value": value, "steps": steps, "warmup": args.warmup,
+        "ms_per_step": ms / steps, "higher_is_better": True,
+        "config": {**cfg.as_dict(), "l2": "inputs larger than L2 (1 GB planes vs 129 MB L2), no flush"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tmul/s", "frac": achieved / peak,
+                     "traffic": None,
+                     "peak_basis": f"integer multiply pipe, {MULS_PER_CLK_SM:.0f} products/clk/SM x {N_SMS} SMs x "
+                                   f"{sm_max:.0f} MHz; {MULS_PER_SITE_SWEEP} Philox products per site update",
+                     "alu_view": {"achieved_tops": alu_ops * N / 2 / t_launch_s / 1e12,
+                                  "peak_tops": ALU_OPS_PER_CLK_SM * N_SMS * sm_max * 1e6 / 1e12,
+                                  "ops_per_site": alu_ops},
+                     "hbm_achieved_gbs": BYTES_PER_SITE_SWEEP * N / 2 / t_launch_s / 1e9,
+                     "hbm_peak_gbs": peaks.get("hbm_gbs", 6800.0)},
+        "cpu_baseline": cpu, "gpu_launches": 2 * steps, "clocks": clocks}))
+
+
+def run_binder3d(args) -> None:
+    """3D physics check: U4(beta) for L = 64, 128, 256 near beta_c of the cubic lattice;
+    curves of consecutive sizes cross at beta_c up to finite-size corrections.  One
+    handle per lattice, each on its own stream so that the small lattices overlap."""
+    import torch
+
+    from paper_1903_11714_gb300 import ising, workloads
+
+    sweeps = args.binder3d_sweeps
+    burn = sweeps // 10
+    lats = workloads.cubic_binder_scan(sweeps)
+    streams = [torch.cuda.Stream() for _ in lats]
+    hs = [ising.Lattice3D(l.L, l.beta, l.seed, l.start, stream=st) for l, st in zip(lats, streams)]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    chunk = 1000
+    for done in range(0, sweeps, chunk):
+        for h in hs:
+            h.sweep(min(chunk, sweeps - done))
+    for h in hs:
+        h.synchronize()
+    dt = time.perf_counter() - t0
+    table = {}
+    for l, h in zip(lats, hs):
+        m = h.moments(burn)
+        table.setdefault(l.L, []).append((l.beta / workloads.BETA_C3, m["binder"], m["abs_m"], m["e"]))
+        h.close()
+    crossings = {}
+    Ls = sorted(table)
+    for L1, L2 in zip(Ls, Ls[1:]):
+        a, c = sorted(table[L1]), sorted(table[L2])
+        d = [(p[0], p[1] - q[1]) for p, q in zip(a, c)]
+        for (b0, d0), (b1, d1) in zip(d, d[1:]):
+            if d0 * d1 <= 0 and d0 != d1:
+                crossings[f"{L1}-{L2}"] = b0 + (b1 - b0) * d0 / (d0 - d1)
+                break
+    flips = sweeps * sum(l.L ** 3 for l in lats)
+    print(json.dumps({"metric": "3D Binder-parameter scan: U4 vs beta/beta_c (cubic lattice)", "workload": "binder3d",
+                      "unit": UNIT, "value": flips / (dt * 1e9), "sweeps": sweeps, "burn_in": burn,
+                      "beta_c": workloads.BETA_C3, "crossing_beta_over_beta_c": crossings,
+                      "U4": {str(L): [[round(b, 4), u] for b, u, _, _ in sorted(v)] for L, v in table.items()},
+                      "e": {str(L): [[round(b, 4), e] for b, _, _, e in sorted(v)] for L, v in table.items()},
+                      "note": "wall clock over all lattices (separate streams); value is aggregate flips/ns"}))
+
+
+def cubic_cpu_baseline(beta: float, seed: int, L: int = 256) -> dict:
+    """The 3D oracle as it stands: one sweep of an L = 256 cube (1.7e7 sites)."""
+    import oracle
+
+    s = oracle.init3d((L, L, L), seed, oracle.HOT)
+    t0 = time.perf_counter()
+    oracle.run3d((L, L, L), beta, seed, sweeps=1, state=s)
+    dt = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": L ** 3 / (dt * 1e9), "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"one sweep of a {L}^3 cube at the same beta (3D oracle, OpenMP)"}
+
+
 def run_binder(args) -> None:
     """Physics validation: U4(T) and <|m|>(T) for L = 64..512 from one batch; the
     curves of different L cross near T_c (the paper's Fig. 3, reduced)."""
@@ -404,9 +519,11 @@ def main() -> None:
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--ref-rows", type=int, default=1024)
-    ap.add_argument("--workload", choices=["single_large", "single_small", "scan", "uneven", "serve", "binder"],
+    ap.add_argument("--workload", choices=["single_large", "single_small", "scan", "uneven", "serve", "binder",
+                                           "cubic", "binder3d"],
                     default="single_large")
     ap.add_argument("--binder-sweeps", type=int, default=1_000_000)
+    ap.add_argument("--binder3d-sweeps", type=int, default=100_000)
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--serve-calib", type=int, default=150)
     ap.add_argument("--serve-slots", type=int, default=256)
@@ -429,7 +546,8 @@ def main() -> None:
     torch.cuda.set_device(local)
     if args.workload != "single_large":
         libbuild.build()
-        {"single_small": run_single_small, "serve": run_serve, "binder": run_binder}.get(
+        {"single_small": run_single_small, "serve": run_serve, "binder": run_binder, "cubic": run_cubic,
+         "binder3d": run_binder3d}.get(
             args.workload, lambda a: run_batched(a, args.workload))(args)
         return
     dist = None

@@ -14,7 +14,7 @@
  * sweep count):
  *   - uniform draw of site (i,j) of colour c in sweep s: output word (p & 3) of
  *     Philox4x32-10 (Salmon et al., SC'11) with key (seed lo32, seed hi32) and
- *     counter (q lo32, q hi32, s, c), where p = i*(L/2) + (j>>1), q = p >> 2;
+ *     counter (s, q lo32, c, q hi32), where p = i*(L/2) + (j>>1), q = p >> 2;
  *   - flip iff h <= 0, or word < T_h with T_h = min(2^32, ceil(exp(-2 beta h) 2^32))
  *     computed on the host in FP64 (see ising_thresholds);
  *   - hot start: sigma = +1 iff the word drawn with s = 0xFFFFFFFF is < 2^31;
@@ -158,6 +158,38 @@ int ising_synchronize(ising_t h);
 
 /* Releases the handle and its device memory (NULL is a no-op). */
 int ising_free(ising_t h);
+
+/* ------------------------------------------------------------------------
+ * Three-dimensional lattice.  Sec. 3 writes the Hamiltonian for a
+ * d-dimensional hypercubic lattice and the Conclusion states that the
+ * checkerboard algorithm carries over to three dimensions; these handles run
+ * that generalisation on the cubic L x L x L torus: colour c = (i+j+k) & 1
+ * (black first), nn = sum of the six neighbours, h = sigma * nn, flip iff
+ * h <= 0 or the site's uniform word is below T_h, h = 2, 4, 6.  E = H(sigma)
+ * over the 3N bonds.  Uniform of site (i,j,k): output word (p & 3) of
+ * Philox4x32-10 with key (seed lo32, seed hi32) and counter
+ * (s, q lo32, c, q hi32), p = (i*L + j)*(L/2) + (k>>1), q = p >> 2 -- the 2D
+ * keying with row index i*L + j.  Hot start as in 2D.
+ * ---------------------------------------------------------------------- */
+
+/*
+ * T[0], T[1], T[2] for h = 2, 4, 6: T_h = min(2^32, ceil(exp(-2 beta h) 2^32))
+ * in host FP64 (T[0], T[1] equal ising_thresholds).  Host-only.  Errors: EINVAL.
+ */
+int ising_thresholds3d(double beta, uint64_t T[3]);
+
+/*
+ * Creates a bit-packed cubic lattice of side L (L % 64 == 0, 64 <= L <= 8192):
+ * device memory L^3/8 bytes of planes plus 16 bytes of history per sweep.
+ * start and stream as in ising_init_ex.  The handle works with ising_sweep,
+ * ising_observables, ising_history, ising_moments (N = L^3), ising_get_lattice
+ * (out[L^3], index (i*L + j)*L + k), ising_get_planes / ising_set_planes (L*L
+ * rows of L/64 words each per colour, row i*L + j; bit b of word w is the site
+ * (i, j, 2(32w+b) + ((i+j+c)&1))), the checkpoint calls, ising_synchronize and
+ * ising_free; ising_set_lattice returns EINVAL.
+ * Errors: EINVAL (L, beta, start), ENOMEM, ECUDA.
+ */
+int ising_init3d(ising_t *out, int64_t L, double beta, uint64_t seed, int start, void *stream);
 
 /* ------------------------------------------------------------------------
  * Batch: many packed lattices of uneven L and beta swept by one persistent

@@ -39,7 +39,7 @@ _lib = None
 _lock = threading.Lock()
 
 HOT, COLD = 0, 1
-INIT_SWEEP = 0xFFFFFFFF  # counter word 2 reserved for the hot start
+INIT_SWEEP = 0xFFFFFFFF  # sweep slot (counter word 0) reserved for the hot start
 
 
 def build(force: bool = False) -> str:
@@ -209,8 +209,14 @@ def half_sweep_rows(s: np.ndarray, c: int, beta: float, seed: int, sweep: int, r
 
 
 def lattice_hash(s: np.ndarray) -> str:
-    """SHA-256 of the row-major lattice with +1 -> 0x01 and -1 -> 0x00."""
-    return hashlib.sha256((np.asarray(s) > 0).astype(np.uint8).tobytes()).hexdigest()
+    """SHA-256 of the row-major lattice with +1 -> 0x01 and -1 -> 0x00 (2D or 3D),
+    fed in slices of the first axis so that large lattices need no full-size copy."""
+    a = np.asarray(s)
+    h = hashlib.sha256()
+    step = max(1, (1 << 28) // max(1, a[0].size))
+    for i in range(0, a.shape[0], step):
+        h.update((a[i:i + step] > 0).astype(np.uint8).tobytes())
+    return h.hexdigest()
 
 
 def moments_exact(M, E, N: int, burn_in: int) -> dict:

@@ -24,7 +24,7 @@
  *     p = exp(-2 beta h) evaluated in FP64 by the host libm.  h <= 0 always flips.
  *   - Site (i,j) of colour c has colour-plane index p = i*(L/2) + (j>>1).  Its
  *     word is output word (p & 3) of Philox with key = (seed low 32, seed high 32)
- *     and counter = (q low 32, q high 32, sweep, c), q = p >> 2.
+ *     and counter = (sweep, q low 32, c, q high 32), q = p >> 2.
  *   - Hot start: sigma = +1 iff the Philox word drawn with sweep = 0xFFFFFFFF is
  *     below 2^31.  Cold start: all +1.
  *   - M = sum sigma; E = -sum_{i,j} sigma[i][j] (sigma[i+1][j] + sigma[i][j+1]),
@@ -110,7 +110,7 @@ static uint32_t site_word(int64_t L, int64_t i, int64_t j, uint64_t seed, uint32
 {
     uint64_t p = (uint64_t)i * (uint64_t)(L / 2) + (uint64_t)(j >> 1);
     uint64_t q = p >> 2;
-    uint32_t ctr[4] = {(uint32_t)q, (uint32_t)(q >> 32), sweep, (uint32_t)c};
+    uint32_t ctr[4] = {sweep, (uint32_t)q, (uint32_t)c, (uint32_t)(q >> 32)};
     uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
     uint32_t out[4];
     oracle_philox4x32_10(ctr, key, out);
@@ -177,7 +177,7 @@ static int64_t half_sweep(int8_t *s, int64_t L, int c, uint64_t T2, uint64_t T4,
                 uint64_t p = (uint64_t)i * (uint64_t)(L / 2) + (uint64_t)(j >> 1);
                 uint64_t q = p >> 2;
                 if (q != cached_q) {
-                    uint32_t ctr[4] = {(uint32_t)q, (uint32_t)(q >> 32), sweep, (uint32_t)c};
+                    uint32_t ctr[4] = {sweep, (uint32_t)q, (uint32_t)c, (uint32_t)(q >> 32)};
                     uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
                     oracle_philox4x32_10(ctr, key, cached);
                     cached_q = q;
@@ -325,7 +325,7 @@ ORACLE_API int64_t oracle_half_sweep_rows(int8_t *s, int64_t L, int c, double be
             uint64_t p = (uint64_t)i * (uint64_t)(L / 2) + (uint64_t)(j >> 1);
             uint64_t q = p >> 2;
             if (q != cached_q) {
-                uint32_t ctr[4] = {(uint32_t)q, (uint32_t)(q >> 32), sweep, (uint32_t)c};
+                uint32_t ctr[4] = {sweep, (uint32_t)q, (uint32_t)c, (uint32_t)(q >> 32)};
                 uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
                 oracle_philox4x32_10(ctr, key, cached);
                 cached_q = q;

@@ -13,6 +13,7 @@
 
 #include "ising.h"
 #include "ising_internal.cuh"
+#include "sweep3d.cuh"
 
 using namespace ising;
 
@@ -52,11 +53,16 @@ constexpr uint32_t kNoTarget = 0xFFFFFFFFu;
 constexpr int64_t kMaxSweeps = 0xFFFFFFFEll;  // sweep counter is a 32-bit Philox counter word
 constexpr int64_t kStageCapBytes = 100 * 1024;  // per pipeline stage (two stages per CTA)
 
-// Acceptance thresholds T_h = min(2^32, ceil(exp(-2 beta h) 2^32)), h = 2, 4.
-bool thresholds(double beta, uint64_t T[2])
+// Handle kind of a cubic (3D) lattice; the public kernel ids are ISING_PACKED
+// and ISING_INT8 (2D).
+constexpr int kKernelCubic = 2;
+
+// Acceptance thresholds T_h = min(2^32, ceil(exp(-2 beta h) 2^32)), h = 2, 4
+// (and h = 6 when n = 3, for the cubic lattice).
+bool thresholds(double beta, uint64_t* T, int n = 2)
 {
     if (!std::isfinite(beta) || beta < 0.0) return false;
-    for (int k = 0; k < 2; ++k) {
+    for (int k = 0; k < n; ++k) {
         const double p = std::exp(-2.0 * beta * (double)(2 * (k + 1)));
         double t = std::ceil(p * 4294967296.0);
         if (t > 4294967296.0) t = 4294967296.0;
@@ -355,7 +361,7 @@ struct ising_s {
     int kernel = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
-    uint64_t T[2] = {0, 0};
+    uint64_t T[3] = {0, 0, 0};
     Engine eng;          // packed
     LatticeDesc desc{};  // host mirror (packed)
     uint32_t* planes = nullptr;
@@ -420,6 +426,57 @@ int check_handle(ising_t h)
     return ISING_OK;
 }
 
+// Words of one colour plane: L rows (2D) or L*L rows (3D) of L/64 words.
+int64_t plane_words(ising_t h)
+{
+    return (h->kernel == kKernelCubic ? h->L * h->L : h->L) * (h->L / 64);
+}
+
+// Sites of the lattice: L^2 or L^3.
+int64_t site_count(ising_t h) { return (h->kernel == kKernelCubic ? h->L : 1) * h->L * h->L; }
+
+uint32_t thr32(uint64_t T) { return T >= 4294967296ull ? 0xFFFFFFFFu : (uint32_t)T; }
+uint32_t all32(uint64_t T) { return T >= 4294967296ull ? 0xFFFFFFFFu : 0u; }
+
+CubicDesc cubic_desc(ising_t h)
+{
+    CubicDesc d{};
+    d.plane[0] = h->planes;
+    d.plane[1] = h->planes + plane_words(h);
+    d.hist = h->hist;
+    d.key = h->seed;
+    d.L = (int32_t)h->L;
+    d.W = (int32_t)(h->L / 64);
+    d.t2 = thr32(h->T[0]);
+    d.t4 = thr32(h->T[1]);
+    d.t6 = thr32(h->T[2]);
+    d.all2 = all32(h->T[0]);
+    d.all4 = all32(h->T[1]);
+    d.all6 = all32(h->T[2]);
+    return d;
+}
+
+// int8 copy of a cubic lattice, index (i*L + j)*L + k, through a bounded staging buffer.
+int cubic_to_host(ising_t h, int8_t* out)
+{
+    const int64_t L = h->L, rows = L * L;
+    const int64_t chunk = std::min<int64_t>(rows, std::max<int64_t>(1, (int64_t)(256ll << 20) / L));
+    int8_t* tmp = nullptr;
+    CK(cudaMalloc(&tmp, (size_t)(chunk * L)));
+    for (int64_t r0 = 0; r0 < rows; r0 += chunk) {
+        const int64_t nr = std::min<int64_t>(chunk, rows - r0);
+        cudaError_t e = launch_cubic_unpack(h->planes, h->planes + plane_words(h), tmp, L, r0, nr, h->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(out + r0 * L, tmp, (size_t)(nr * L), cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) {
+            cudaFree(tmp);
+            return cuda_fail(e, "cubic unpack to host");
+        }
+    }
+    cudaFree(tmp);
+    return ISING_OK;
+}
+
 int read_status(ising_t h)
 {
     if (h->kernel == ISING_PACKED) return h->eng.check_status();
@@ -478,7 +535,9 @@ bool spins_valid(const int8_t* in, int64_t n)
 int refresh_me0(ising_t h)
 {
     cudaError_t e;
-    if (h->kernel == ISING_PACKED)
+    if (h->kernel == kKernelCubic)
+        e = launch_cubic_observe(h->planes, h->planes + plane_words(h), h->L, h->d_me0, h->stream);
+    else if (h->kernel == ISING_PACKED)
         e = launch_packed_observe(h->planes, h->planes + h->L * (h->L / 64), h->L, h->d_me0, h->stream);
     else
         e = launch_int8_observe(h->lat, h->L, h->d_me0, h->stream);
@@ -618,6 +677,54 @@ int ising_init(ising_t* out, int64_t L, double beta, uint64_t seed)
     return ising_init_ex(out, L, beta, seed, ISING_HOT, ISING_PACKED, nullptr);
 }
 
+int ising_thresholds3d(double beta, uint64_t T[3])
+{
+    if (!T) return fail(ISING_EINVAL, "null output");
+    uint64_t t[3];
+    if (!thresholds(beta, t, 3)) return fail(ISING_EINVAL, "beta must be finite and >= 0");
+    for (int k = 0; k < 3; ++k) T[k] = t[k];
+    return ISING_OK;
+}
+
+int ising_init3d(ising_t* out, int64_t L, double beta, uint64_t seed, int start, void* stream)
+{
+    if (!out) return fail(ISING_EINVAL, "null output");
+    uint64_t T[3];
+    if (!thresholds(beta, T, 3)) return fail(ISING_EINVAL, "beta must be finite and >= 0");
+    if (start != ISING_HOT && start != ISING_COLD) return fail(ISING_EINVAL, "start must be ISING_HOT or ISING_COLD");
+    if (L < 64 || L % 64 || L > kCubicMaxL)
+        return fail(ISING_EINVAL, "3D lattices need L %% 64 == 0 and 64 <= L <= %lld", (long long)kCubicMaxL);
+    ising_t h = new ising_s();
+    h->L = L;
+    h->beta = beta;
+    h->seed = seed;
+    h->start = start;
+    h->kernel = kKernelCubic;
+    for (int k = 0; k < 3; ++k) h->T[k] = T[k];
+    int rc = make_stream(stream, &h->stream, &h->own_stream);
+    if (rc) {
+        delete h;
+        return rc;
+    }
+    cudaError_t e = cudaMalloc(&h->d_me0, 2 * sizeof(int64_t));
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_mom, 6 * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_sums, 11 * sizeof(uint64_t));
+    if (e == cudaSuccess) e = cudaMalloc(&h->planes, sizeof(uint32_t) * 2 * (size_t)plane_words(h));
+    if (e == cudaSuccess) e = launch_cubic_init(h->planes, h->planes + plane_words(h), L, seed, start, h->stream);
+    rc = (e == cudaSuccess) ? ensure_hist(h, 1024) : cuda_fail(e, "3D lattice set-up");
+    if (!rc) rc = refresh_me0(h);
+    if (!rc) {
+        e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) rc = cuda_fail(e, "3D init");
+    }
+    if (rc) {
+        destroy_handle(h);
+        return rc;
+    }
+    *out = h;
+    return ISING_OK;
+}
+
 int ising_sweep(ising_t h, int64_t n)
 {
     int rc = check_handle(h);
@@ -640,6 +747,13 @@ int ising_sweep(ising_t h, int64_t n)
     } else if (h->kernel == ISING_PACKED) {
         rc = h->eng.run(n, 0);
         if (rc) return rc;
+    } else if (h->kernel == kKernelCubic) {
+        const CubicDesc d = cubic_desc(h);
+        for (int64_t k = 0; k < n; ++k)
+            for (int c = 0; c < 2; ++c) {
+                cudaError_t e = launch_cubic_half_sweep(d, c, (uint32_t)(h->sweeps_done + k), h->stream);
+                if (e != cudaSuccess) return cuda_fail(e, "3D half-sweep launch");
+            }
     } else {
         uint32_t t2, t4, all2, all4;
         LatticeDesc tmp{};
@@ -709,7 +823,7 @@ int ising_moments(ising_t h, int64_t burn_in, double out[6], uint64_t sums[11])
     if (rc) return rc;
     if (!out) return fail(ISING_EINVAL, "null output");
     if (burn_in < 0 || burn_in >= h->sweeps_done) return fail(ISING_EINVAL, "no samples after burn-in");
-    CK(launch_moments(h->hist, burn_in, h->sweeps_done - burn_in, h->L * h->L, h->d_mom, h->d_sums, h->stream));
+    CK(launch_moments(h->hist, burn_in, h->sweeps_done - burn_in, site_count(h), h->d_mom, h->d_sums, h->stream));
     double m[6];
     uint64_t s[11];
     CK(cudaMemcpyAsync(m, h->d_mom, sizeof(m), cudaMemcpyDeviceToHost, h->stream));
@@ -728,6 +842,7 @@ int ising_get_lattice(ising_t h, int8_t* out)
     if (!out) return fail(ISING_EINVAL, "null output");
     rc = read_status(h);
     if (rc) return rc;
+    if (h->kernel == kKernelCubic) return cubic_to_host(h, out);
     if (h->kernel == ISING_PACKED)
         return packed_to_host(h->planes, h->planes + h->L * (h->L / 64), h->L, out, h->stream);
     CK(cudaMemcpyAsync(out, h->lat, (size_t)(h->L * h->L), cudaMemcpyDeviceToHost, h->stream));
@@ -740,6 +855,7 @@ int ising_set_lattice(ising_t h, const int8_t* in)
     int rc = check_handle(h);
     if (rc) return rc;
     if (!in) return fail(ISING_EINVAL, "null input");
+    if (h->kernel == kKernelCubic) return fail(ISING_EINVAL, "set_lattice is for 2D lattices; use set_planes");
     if (!spins_valid(in, h->L * h->L)) return fail(ISING_EINVAL, "lattice entries must be +1 or -1");
     rc = read_status(h);
     if (rc) return rc;
@@ -761,10 +877,10 @@ int ising_get_planes(ising_t h, uint32_t* black, uint32_t* white)
 {
     int rc = check_handle(h);
     if (rc) return rc;
-    if (h->kernel != ISING_PACKED) return fail(ISING_EINVAL, "not a packed handle");
-    const size_t bytes = sizeof(uint32_t) * (size_t)(h->L * (h->L / 64));
+    if (h->kernel == ISING_INT8) return fail(ISING_EINVAL, "not a packed handle");
+    const size_t bytes = sizeof(uint32_t) * (size_t)plane_words(h);
     if (black) CK(cudaMemcpyAsync(black, h->planes, bytes, cudaMemcpyDeviceToHost, h->stream));
-    if (white) CK(cudaMemcpyAsync(white, h->planes + h->L * (h->L / 64), bytes, cudaMemcpyDeviceToHost, h->stream));
+    if (white) CK(cudaMemcpyAsync(white, h->planes + plane_words(h), bytes, cudaMemcpyDeviceToHost, h->stream));
     return read_status(h);
 }
 
@@ -772,11 +888,11 @@ int ising_set_planes(ising_t h, const uint32_t* black, const uint32_t* white)
 {
     int rc = check_handle(h);
     if (rc) return rc;
-    if (h->kernel != ISING_PACKED) return fail(ISING_EINVAL, "not a packed handle");
+    if (h->kernel == ISING_INT8) return fail(ISING_EINVAL, "not a packed handle");
     if (!black || !white) return fail(ISING_EINVAL, "null input");
-    const size_t bytes = sizeof(uint32_t) * (size_t)(h->L * (h->L / 64));
+    const size_t bytes = sizeof(uint32_t) * (size_t)plane_words(h);
     CK(cudaMemcpyAsync(h->planes, black, bytes, cudaMemcpyHostToDevice, h->stream));
-    CK(cudaMemcpyAsync(h->planes + h->L * (h->L / 64), white, bytes, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(h->planes + plane_words(h), white, bytes, cudaMemcpyHostToDevice, h->stream));
     if (h->sweeps_done == 0) {
         rc = refresh_me0(h);
         if (rc) return rc;
@@ -794,7 +910,7 @@ struct CkptHeader {
 };
 int64_t lattice_bytes(ising_t h)
 {
-    return h->kernel == ISING_PACKED ? (int64_t)sizeof(uint32_t) * 2 * h->L * (h->L / 64) : h->L * h->L;
+    return h->kernel == ISING_INT8 ? h->L * h->L : (int64_t)sizeof(uint32_t) * 2 * plane_words(h);
 }
 }  // namespace
 
@@ -829,7 +945,7 @@ int ising_save(ising_t h, void* buf, int64_t bytes)
     char* p = (char*)buf;
     memcpy(p, &hd, sizeof(hd));
     p += sizeof(hd);
-    const void* src = h->kernel == ISING_PACKED ? (const void*)h->planes : (const void*)h->lat;
+    const void* src = h->kernel == ISING_INT8 ? (const void*)h->lat : (const void*)h->planes;
     CK(cudaMemcpyAsync(p, src, (size_t)hd.lattice_bytes, cudaMemcpyDeviceToHost, h->stream));
     p += hd.lattice_bytes;
     CK(cudaMemcpyAsync(p, h->d_me0, 16, cudaMemcpyDeviceToHost, h->stream));
@@ -847,7 +963,8 @@ int ising_load(ising_t* out, const void* buf, int64_t bytes, void* stream)
     memcpy(&hd, buf, sizeof(hd));
     if (memcmp(hd.magic, "ISINGCK1", 8) != 0 || hd.version != 1) return fail(ISING_EINVAL, "not a checkpoint");
     ising_t h = nullptr;
-    int rc = ising_init_ex(&h, hd.L, hd.beta, hd.seed, ISING_COLD, (int)hd.kernel, stream);
+    int rc = hd.kernel == kKernelCubic ? ising_init3d(&h, hd.L, hd.beta, hd.seed, ISING_COLD, stream)
+                                       : ising_init_ex(&h, hd.L, hd.beta, hd.seed, ISING_COLD, (int)hd.kernel, stream);
     if (rc) return rc;
     h->start = (int)hd.start;
     if (hd.lattice_bytes != lattice_bytes(h) ||
@@ -856,7 +973,7 @@ int ising_load(ising_t* out, const void* buf, int64_t bytes, void* stream)
         return fail(ISING_EINVAL, "checkpoint truncated");
     }
     const char* p = (const char*)buf + sizeof(CkptHeader);
-    void* dst = h->kernel == ISING_PACKED ? (void*)h->planes : (void*)h->lat;
+    void* dst = h->kernel == ISING_INT8 ? (void*)h->lat : (void*)h->planes;
     rc = ensure_hist(h, hd.sweeps_done + 1);
     cudaError_t e = cudaSuccess;
     if (!rc) e = cudaMemcpyAsync(dst, p, (size_t)hd.lattice_bytes, cudaMemcpyHostToDevice, h->stream);

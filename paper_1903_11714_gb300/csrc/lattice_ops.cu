@@ -34,7 +34,7 @@ __global__ void packed_init_kernel(uint32_t* black, uint32_t* white, int64_t L, 
         for (int j = 0; j < 8; ++j) {
             const uint64_t q = q0 + j;
             uint32_t x[4];
-            philox4x32_10((uint32_t)q, (uint32_t)(q >> 32), kInitSweep, (uint32_t)c, key, x);
+            site_philox(q, kInitSweep, (uint32_t)c, key, x);
 #pragma unroll
             for (int m = 0; m < 4; ++m) bits |= (x[m] < 0x80000000u ? 1u : 0u) << (4 * j + m);
         }

@@ -1,0 +1,387 @@
+// Three-dimensional checkerboard Metropolis sweep on bit-packed colour planes.
+//
+// The paper's Hamiltonian is written for a d-dimensional hypercubic lattice
+// (Sec. 3) and its conclusion states that the checkerboard algorithm carries
+// over to three dimensions; this file is that generalisation for the cubic
+// L x L x L torus.  Every rule of the 2D sweep is kept (colour order black then
+// white, h = sigma * nn, flip iff h <= 0 or x < T_h, integer thresholds, Philox
+// draws keyed by plane index); the neighbourhood has six sites, so the per-word
+// neighbour count is a 6-input bitwise adder and three thresholds (h = 2, 4, 6)
+// are tested.
+//
+// GB300 mapping: a persistent grid (two 256-thread CTAs per SM) walks groups of
+// four adjacent words (one 16-byte vector load per neighbour row through the
+// read-only path; 128 sites per thread iteration).  The kernel is bound by the
+// integer pipes (Philox), not by memory: a half-sweep moves 3/16 byte per
+// updated site, and the six neighbour rows of a word are re-read from L2.
+#include <cstdint>
+
+#include "ising_internal.cuh"
+#include "philox.cuh"
+#include "sweep3d.cuh"
+
+namespace ising {
+namespace {
+
+constexpr uint32_t kInitSweep3 = 0xFFFFFFFFu;
+constexpr int kThreads3 = 256;
+
+// New value of one 32-site target word from its six neighbour words.
+__device__ __forceinline__ uint32_t update_word3d(uint32_t t, uint32_t up, uint32_t dn, uint32_t no, uint32_t so,
+                                                  uint32_t same, uint32_t hz, uint32_t q_lo, const PhiloxWordConsts& pc,
+                                                  const CubicDesc& d)
+{
+    // anti-aligned neighbour bits and their 6-input sum n = 4*b2 + 2*b1 + b0:
+    // two full adders over three inputs each, then the sum bits added (b0, carry
+    // c3) and the three weight-2 carries added (b1, b2)
+    const uint32_t a0 = t ^ up, a1 = t ^ dn, a2 = t ^ no, a3 = t ^ so, a4 = t ^ same, a5 = t ^ hz;
+    const uint32_t s1 = a0 ^ a1 ^ a2, c1 = (a0 & a1) | (a2 & (a0 ^ a1));
+    const uint32_t s2 = a3 ^ a4 ^ a5, c2 = (a3 & a4) | (a5 & (a3 ^ a4));
+    const uint32_t b0 = s1 ^ s2, c3 = s1 & s2;
+    const uint32_t b1 = c1 ^ c2 ^ c3;
+    const uint32_t b2 = (c1 & c2) | (c3 & (c1 ^ c2));
+
+    uint32_t x[32];
+    philox_word8(q_lo, pc, d.key, x);
+    // threshold tests as carry chains (sub.cc sets the carry iff x >= t; addc
+    // shifts it into the mask), one chain per threshold
+    uint32_t g2 = 0, g4 = 0, g6 = 0;
+#pragma unroll
+    for (int b = 31; b >= 0; --b) {
+        asm("{\n\t.reg .u32 d;\n\tsub.cc.u32 d, %1, %2;\n\taddc.u32 %0, %0, %0;\n\t}" : "+r"(g2) : "r"(x[b]), "r"(d.t2));
+        asm("{\n\t.reg .u32 d;\n\tsub.cc.u32 d, %1, %2;\n\taddc.u32 %0, %0, %0;\n\t}" : "+r"(g4) : "r"(x[b]), "r"(d.t4));
+        asm("{\n\t.reg .u32 d;\n\tsub.cc.u32 d, %1, %2;\n\taddc.u32 %0, %0, %0;\n\t}" : "+r"(g6) : "r"(x[b]), "r"(d.t6));
+    }
+    const uint32_t q2 = d.all2 | ~g2, q4 = d.all4 | ~g4, q6 = d.all6 | ~g6;
+    // h = 6 - 2n: n >= 3 (h <= 0) always; n = 2 (h = 2): x < T2; n = 1 (h = 4):
+    // x < T4; n = 0 (h = 6): x < T6.  T6 <= T4 <= T2, so q6 is inside q4 inside q2
+    // and each of q2, q4, q6 may be ORed over a superset of its own class.
+    const uint32_t flip = b2 | (b1 & (b0 | q2)) | (b0 & q4) | q6;
+    return t ^ flip;
+}
+
+template <int G>
+__device__ __forceinline__ void load_ro(const uint32_t* p, uint32_t v[G])
+{
+    if constexpr (G == 4) {
+        const uint4 q = __ldg(reinterpret_cast<const uint4*>(p));
+        v[0] = q.x;
+        v[1] = q.y;
+        v[2] = q.z;
+        v[3] = q.w;
+    } else {
+#pragma unroll
+        for (int k = 0; k < G; ++k) v[k] = __ldg(p + k);
+    }
+}
+
+// The source-colour neighbours of G adjacent target words (w .. w+G-1) of row
+// (i, j): rows (i+-1, j) and (i, j+-1) at the same words, and the row's own
+// source words, same (bit b <-> same m) and hz (bit b <-> m - 1 or m + 1).
+template <int G>
+struct Nbr {
+    uint32_t up[G], dn[G], no[G], so[G], sm[G], hz[G];
+};
+
+template <int G>
+__device__ __forceinline__ void load_neighbours(const uint32_t* __restrict__ src, int64_t L, int W, int64_t i,
+                                                int64_t j, int w, int par, Nbr<G>& n)
+{
+    const int64_t im = (i == 0) ? L - 1 : i - 1, ip = (i == L - 1) ? 0 : i + 1;
+    const int64_t jm = (j == 0) ? L - 1 : j - 1, jp = (j == L - 1) ? 0 : j + 1;
+    const uint32_t* row = src + (i * L + j) * W;
+    load_ro<G>(src + (im * L + j) * W + w, n.up);
+    load_ro<G>(src + (ip * L + j) * W + w, n.dn);
+    load_ro<G>(src + (i * L + jm) * W + w, n.no);
+    load_ro<G>(src + (i * L + jp) * W + w, n.so);
+    load_ro<G>(row + w, n.sm);
+    if (par) {  // target at odd k: z-neighbours at source m and m + 1
+        const uint32_t next = __ldg(row + ((w + G == W) ? 0 : w + G));
+#pragma unroll
+        for (int k = 0; k < G; ++k) n.hz[k] = __funnelshift_r(n.sm[k], k + 1 < G ? n.sm[k + 1] : next, 1);
+    } else {  // target at even k: z-neighbours at source m - 1 and m
+        const uint32_t prev = __ldg(row + ((w == 0) ? W - 1 : w - 1));
+#pragma unroll
+        for (int k = 0; k < G; ++k) n.hz[k] = __funnelshift_l(k > 0 ? n.sm[k - 1] : prev, n.sm[k], 1);
+    }
+}
+
+// The same from the word offsets of the five source rows (row, i-1, i+1, j-1, j+1).
+template <int G>
+__device__ __forceinline__ void load_neighbours_at(const uint32_t* __restrict__ src, int W, int64_t row,
+                                                   int64_t up, int64_t dn, int64_t no, int64_t so, int w, int par,
+                                                   Nbr<G>& n)
+{
+    const uint32_t* rp = src + row;
+    load_ro<G>(src + up + w, n.up);
+    load_ro<G>(src + dn + w, n.dn);
+    load_ro<G>(src + no + w, n.no);
+    load_ro<G>(src + so + w, n.so);
+    load_ro<G>(rp + w, n.sm);
+    if (par) {
+        const uint32_t next = __ldg(rp + ((w + G == W) ? 0 : w + G));
+#pragma unroll
+        for (int k = 0; k < G; ++k) n.hz[k] = __funnelshift_r(n.sm[k], k + 1 < G ? n.sm[k + 1] : next, 1);
+    } else {
+        const uint32_t prev = __ldg(rp + ((w == 0) ? W - 1 : w - 1));
+#pragma unroll
+        for (int k = 0; k < G; ++k) n.hz[k] = __funnelshift_l(k > 0 ? n.sm[k - 1] : prev, n.sm[k], 1);
+    }
+}
+
+// Block sum of two per-thread counts, then 2x the sums added to out[0..1].
+template <int NT>
+__device__ __forceinline__ void block_add_twice(unsigned long long a, unsigned long long b,
+                                                unsigned long long* red, int64_t* out)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        b += __shfl_down_sync(0xffffffffu, b, o);
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+        red[2 * warp] = a;
+        red[2 * warp + 1] = b;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long sa = 0, sb = 0;
+        for (int k = 0; k < NT / 32; ++k) {
+            sa += red[2 * k];
+            sb += red[2 * k + 1];
+        }
+        atomicAdd(reinterpret_cast<unsigned long long*>(out), 2ull * sa);
+        atomicAdd(reinterpret_cast<unsigned long long*>(out + 1), 2ull * sb);
+    }
+}
+
+template <int NT, int G>
+__global__ void __launch_bounds__(NT, 2) cubic_half_sweep_kernel(const __grid_constant__ CubicDesc d, int colour,
+                                                                 uint32_t sweep)
+{
+    __shared__ unsigned long long red[2 * (NT / 32)];
+    const int64_t L = d.L;
+    const int W = d.W, WG = W / G;
+    const int64_t ngroups = L * L * WG;
+    const uint32_t* __restrict__ src = d.plane[colour ^ 1];
+    uint32_t* __restrict__ tgt = d.plane[colour];
+    if (colour == 0 && blockIdx.x == 0 && threadIdx.x == 0) {
+        // open this sweep's (M, E) slot: M = 2 * ups - N, E = 2 * anti - 3N
+        const int64_t N = L * L * L;
+        d.hist[2 * (int64_t)sweep] = -N;
+        d.hist[2 * (int64_t)sweep + 1] = -3 * N;
+    }
+    const bool q_small = cubic_q_small(L);
+    const PhiloxWordConsts pc_all = philox_consts(d.key, 0u, sweep, (uint32_t)colour);
+    // per-thread counts stay below 2^32: a thread sees at most L^3 / (2 * 152 * 2 * 256)
+    // white sites (< 4e6 at L = 8192) with at most 7 counted bits each
+    uint32_t ups = 0, anti = 0;
+    // (i, j, word group) of g = start + k * stride, advanced without divisions: the
+    // stride is step_w groups within a row plus step_r rows, step_r = step_i * L + step_j
+    const int64_t start = (int64_t)blockIdx.x * NT + threadIdx.x;
+    const int64_t stride = (int64_t)gridDim.x * NT;
+    const int64_t step_r = stride / WG;
+    const int step_w = (int)(stride - step_r * WG);
+    const int64_t step_i = step_r / L, step_j = step_r - step_i * L;
+    int64_t i = 0, j = 0;
+    int wg = 0;
+    if (start < ngroups) {
+        const int64_t r0 = start / WG;
+        wg = (int)(start - r0 * WG);
+        i = r0 / L;
+        j = r0 - i * L;
+    }
+    // word offset of row (i, j), carried along the walk, and the offsets from it to
+    // the rows (i-+1, j) and (i, j-+1) away from / across the torus seam
+    const int64_t Wl = W, LW = L * Wl, LLW = L * LW;
+    const int64_t step_off = step_r * Wl;
+    int64_t row = (i * L + j) * Wl;
+    for (int64_t g = start; g < ngroups; g += stride) {
+        const int w = wg * G;
+        const int par = (int)((i + j + colour) & 1);
+        const int64_t up = row + (i == 0 ? LLW - LW : -LW), dn = row + (i == L - 1 ? LW - LLW : LW);
+        const int64_t no = row + (j == 0 ? LW - Wl : -Wl), so = row + (j == L - 1 ? Wl - LW : Wl);
+        Nbr<G> n;
+        load_neighbours_at<G>(src, W, row, up, dn, no, so, w, par, n);
+        uint32_t* trow = tgt + row + w;
+        uint32_t t[G];
+        if constexpr (G == 4) {
+            const uint4 q = *reinterpret_cast<const uint4*>(trow);
+            t[0] = q.x;
+            t[1] = q.y;
+            t[2] = q.z;
+            t[3] = q.w;
+        } else {
+#pragma unroll
+            for (int k = 0; k < G; ++k) t[k] = trow[k];
+        }
+        // q0 = r * (L/8) + 8w = 8 * (row + w) with L/8 = 8W; it is a multiple of 8 * G,
+        // so the group's calls q0 .. q0 + 8G - 1 share q's high word
+        const uint64_t q0 = 8ull * (uint64_t)(row + w);
+        const PhiloxWordConsts pc =
+            q_small ? pc_all : philox_consts(d.key, (uint32_t)(q0 >> 32), sweep, (uint32_t)colour);
+        uint32_t nw[G];
+#pragma unroll
+        for (int k = 0; k < G; ++k)
+            nw[k] = update_word3d(t[k], n.up[k], n.dn[k], n.no[k], n.so[k], n.sm[k], n.hz[k], (uint32_t)q0 + 8u * k,
+                                  pc, d);
+        if constexpr (G == 4) {
+            *reinterpret_cast<uint4*>(trow) = make_uint4(nw[0], nw[1], nw[2], nw[3]);
+        } else {
+#pragma unroll
+            for (int k = 0; k < G; ++k) trow[k] = nw[k];
+        }
+        if (colour == 1) {
+#pragma unroll
+            for (int k = 0; k < G; ++k) {
+                ups += __popc(nw[k]) + __popc(n.sm[k]);
+                anti += __popc(nw[k] ^ n.up[k]) + __popc(nw[k] ^ n.dn[k]) + __popc(nw[k] ^ n.no[k]) +
+                        __popc(nw[k] ^ n.so[k]) + __popc(nw[k] ^ n.sm[k]) + __popc(nw[k] ^ n.hz[k]);
+            }
+        }
+        wg += step_w;
+        j += step_j;
+        i += step_i;
+        row += step_off;
+        if (wg >= WG) {
+            wg -= WG;
+            ++j;
+            row += Wl;
+        }
+        if (j >= L) {
+            j -= L;
+            ++i;
+        }
+    }
+    if (colour == 1) block_add_twice<NT>(ups, anti, red, d.hist + 2 * (int64_t)sweep);
+}
+
+// (M, E) of a state: every bond joins a black and a white site, so counting the
+// white sites' six anti-aligned neighbours counts each anti-aligned bond once.
+template <int NT, int G>
+__global__ void __launch_bounds__(NT) cubic_observe_kernel(const uint32_t* __restrict__ black,
+                                                           const uint32_t* __restrict__ white, int64_t L,
+                                                           int64_t* ME)
+{
+    __shared__ unsigned long long red[2 * (NT / 32)];
+    const int W = (int)(L / 64), WG = W / G;
+    const int64_t ngroups = L * L * WG;
+    unsigned long long ups = 0, anti = 0;
+    for (int64_t g = (int64_t)blockIdx.x * NT + threadIdx.x; g < ngroups; g += (int64_t)gridDim.x * NT) {
+        const int64_t r = g / WG;
+        const int w = (int)(g - r * WG) * G;
+        const int64_t i = r / L, j = r - i * L;
+        Nbr<G> n;
+        load_neighbours<G>(black, L, W, i, j, w, (int)((i + j + 1) & 1), n);
+        uint32_t t[G];
+        load_ro<G>(white + r * W + w, t);
+#pragma unroll
+        for (int k = 0; k < G; ++k) {
+            ups += __popc(t[k]) + __popc(n.sm[k]);
+            anti += __popc(t[k] ^ n.up[k]) + __popc(t[k] ^ n.dn[k]) + __popc(t[k] ^ n.no[k]) + __popc(t[k] ^ n.so[k]) +
+                    __popc(t[k] ^ n.sm[k]) + __popc(t[k] ^ n.hz[k]);
+        }
+    }
+    block_add_twice<NT>(ups, anti, red, ME);
+}
+
+__global__ void cubic_set_pair(int64_t* p, int64_t a, int64_t b)
+{
+    p[0] = a;
+    p[1] = b;
+}
+
+// Start state: hot = bit (x < 2^31) of the draw with sweep slot 0xFFFFFFFF; cold = all +1.
+__global__ void cubic_init_kernel(uint32_t* black, uint32_t* white, int64_t L, uint64_t key, int start)
+{
+    const int64_t W = L / 64, words = L * L * W;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < 2 * words;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int c = idx >= words;
+        const int64_t e = idx - c * words;
+        uint32_t* plane = c ? white : black;
+        if (start == 1) {
+            plane[e] = 0xFFFFFFFFu;
+            continue;
+        }
+        const int64_t r = e / W, w = e - r * W;
+        const uint64_t q0 = (uint64_t)r * (uint64_t)(L / 8) + 8ull * (uint64_t)w;
+        uint32_t bits = 0;
+        for (int j = 0; j < 8; ++j) {
+            uint32_t x[4];
+            site_philox(q0 + j, kInitSweep3, (uint32_t)c, key, x);
+#pragma unroll
+            for (int m = 0; m < 4; ++m) bits |= (x[m] < 0x80000000u ? 1u : 0u) << (4 * j + m);
+        }
+        plane[e] = bits;
+    }
+}
+
+__global__ void cubic_unpack_kernel(const uint32_t* __restrict__ black, const uint32_t* __restrict__ white,
+                                    int8_t* lat, int64_t L, int64_t row0, int64_t nrows)
+{
+    const int64_t W = L / 64;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < nrows * W;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t a = idx / W, w = idx - a * W;
+        const int64_t r = row0 + a, i = r / L, j = r - i * L;
+        const uint32_t bw[2] = {black[r * W + w], white[r * W + w]};
+        int8_t* out = lat + a * L + 64 * w;
+        for (int c = 0; c < 2; ++c) {
+            const int off = (int)((i + j + c) & 1);
+            for (int b = 0; b < 32; ++b) out[2 * b + off] = ((bw[c] >> b) & 1u) ? (int8_t)1 : (int8_t)-1;
+        }
+    }
+}
+
+int grid3(int64_t work, int threads)
+{
+    const int64_t want = (work + threads - 1) / threads;
+    const int64_t cap = (int64_t)sm_count() * 16;
+    return (int)(want < 1 ? 1 : (want > cap ? cap : want));
+}
+
+}  // namespace
+
+cudaError_t launch_cubic_init(uint32_t* black, uint32_t* white, int64_t L, uint64_t key, int start, cudaStream_t s)
+{
+    cubic_init_kernel<<<grid3(2 * L * L * (L / 64), 256), 256, 0, s>>>(black, white, L, key, start);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cubic_observe(const uint32_t* black, const uint32_t* white, int64_t L, int64_t* ME,
+                                 cudaStream_t s)
+{
+    cubic_set_pair<<<1, 1, 0, s>>>(ME, -L * L * L, -3 * L * L * L);
+    const int64_t W = L / 64;
+    if (W % 4 == 0)
+        cubic_observe_kernel<256, 4><<<grid3(L * L * W / 4, 256), 256, 0, s>>>(black, white, L, ME);
+    else
+        cubic_observe_kernel<256, 1><<<grid3(L * L * W, 256), 256, 0, s>>>(black, white, L, ME);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cubic_half_sweep(const CubicDesc& d, int colour, uint32_t sweep, cudaStream_t s)
+{
+    const int64_t L = d.L, W = d.W;
+    const int G = (W % 4 == 0) ? 4 : 1;
+    const int64_t groups = L * L * (W / G);
+    const int64_t resident = 2 * (int64_t)sm_count();
+    const int64_t need = (groups + kThreads3 - 1) / kThreads3;
+    const int grid = (int)(need < resident ? need : resident);
+    if (G == 4)
+        cubic_half_sweep_kernel<kThreads3, 4><<<grid, kThreads3, 0, s>>>(d, colour, sweep);
+    else
+        cubic_half_sweep_kernel<kThreads3, 1><<<grid, kThreads3, 0, s>>>(d, colour, sweep);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cubic_unpack(const uint32_t* black, const uint32_t* white, int8_t* lat, int64_t L, int64_t row0,
+                                int64_t nrows, cudaStream_t s)
+{
+    cubic_unpack_kernel<<<grid3(nrows * (L / 64), 256), 256, 0, s>>>(black, white, lat, L, row0, nrows);
+    return cudaGetLastError();
+}
+
+}  // namespace ising

@@ -34,7 +34,7 @@ __global__ void int8_init_kernel(int8_t* lat, int64_t L, uint64_t key, int start
             const uint64_t q = (uint64_t)i * (uint64_t)(L / 8) + (uint64_t)g;
             for (int c = 0; c < 2; ++c) {
                 uint32_t x[4];
-                philox4x32_10((uint32_t)q, (uint32_t)(q >> 32), kInitSweep, (uint32_t)c, key, x);
+                site_philox(q, kInitSweep, (uint32_t)c, key, x);
                 const int r = (int)((i + c) & 1);
                 for (int b = 0; b < 4; ++b) {
                     const uint64_t byte = x[b] < 0x80000000u ? 0x01ull : 0xFFull;
@@ -187,7 +187,7 @@ __global__ void int8_half_sweep_chunk8_kernel(int8_t* lat, int64_t L, uint64_t k
 
         const uint64_t q = (uint64_t)i * (uint64_t)(L / 8) + (uint64_t)g;
         uint32_t x[4];
-        philox4x32_10((uint32_t)q, (uint32_t)(q >> 32), sweep, (uint32_t)colour, key, x);
+        site_philox(q, sweep, (uint32_t)colour, key, x);
 
         uint64_t nv = cur;
         long long e_here = 0;

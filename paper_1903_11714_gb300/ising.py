@@ -4,8 +4,8 @@ Argument marshalling only: every function forwards to the C entry point of the
 same name, and every step of the sweep runs in the library's CUDA kernels.  If
 the library has not been built, ``lib()`` raises -- there is no fallback.
 
-``Lattice`` and ``Batch`` are small owners of an ``ising_t`` / ``ising_batch_t``
-handle that call the same entry points.  Streams may be given as a
+``Lattice``, ``Lattice3D`` and ``Batch`` are small owners of an ``ising_t`` /
+``ising_batch_t`` handle that call the same entry points.  Streams may be given as a
 ``torch.cuda.Stream``, a raw ``cudaStream_t`` integer, or None (the handle then
 creates its own stream).
 """
@@ -23,6 +23,7 @@ LIB_PATH = os.path.join(HERE, "libising_gb300.so")
 ISING_OK, ISING_EINVAL, ISING_ENOMEM, ISING_ECUDA, ISING_ETIMEOUT, ISING_EBUSY = 0, -1, -2, -3, -4, -5
 HOT, COLD = 0, 1
 PACKED, INT8 = 0, 1
+CUBIC = 2  # kernel id recorded in checkpoints of 3D handles
 
 # Entry points declared in include/ising.h: name -> (restype, argtypes)
 _vp = ctypes.c_void_p
@@ -50,6 +51,8 @@ _SIGS = {
     "ising_load": (ctypes.c_int, [_P(_vp), _vp, _i64, _vp]),
     "ising_synchronize": (ctypes.c_int, [_vp]),
     "ising_free": (ctypes.c_int, [_vp]),
+    "ising_thresholds3d": (ctypes.c_int, [_d, _P(_u64)]),
+    "ising_init3d": (ctypes.c_int, [_P(_vp), _i64, _d, _u64, ctypes.c_int, _vp]),
     "ising_batch_create": (ctypes.c_int, [_P(_vp), _i32, _i64, _i64, _i32, _vp]),
     "ising_batch_add": (ctypes.c_int, [_vp, _i64, _d, _u64, _i32, _i64, _i32, _P(_i32)]),
     "ising_batch_remove": (ctypes.c_int, [_vp, _i32]),
@@ -179,8 +182,20 @@ def ising_moments(h: int, burn_in: int) -> dict:
     return _moments_dict(out, sums)
 
 
-def ising_get_lattice(h: int, L: int) -> np.ndarray:
-    out = np.empty((L, L), dtype=np.int8)
+def ising_thresholds3d(beta: float) -> tuple[int, int, int]:
+    T = np.zeros(3, dtype=np.uint64)
+    _check(lib().ising_thresholds3d(float(beta), _ptr(T, ctypes.c_uint64)))
+    return int(T[0]), int(T[1]), int(T[2])
+
+
+def ising_init3d(L: int, beta: float, seed: int, start: int = HOT, stream=None) -> int:
+    h = ctypes.c_void_p()
+    _check(lib().ising_init3d(ctypes.byref(h), int(L), float(beta), int(seed), int(start), _stream_ptr(stream)))
+    return h.value
+
+
+def ising_get_lattice(h: int, L: int, dim: int = 2) -> np.ndarray:
+    out = np.empty((L,) * dim, dtype=np.int8)
     _check(lib().ising_get_lattice(h, _ptr(out, ctypes.c_int8)))
     return out
 
@@ -191,11 +206,12 @@ def ising_set_lattice(h: int, lattice: np.ndarray) -> None:
 
 
 def ising_get_planes(h: int, L: int, black: np.ndarray | None = None,
-                     white: np.ndarray | None = None) -> tuple[np.ndarray, np.ndarray]:
-    b = np.empty(L * (L // 64), dtype=np.uint32) if black is None else black
-    w = np.empty(L * (L // 64), dtype=np.uint32) if white is None else white
+                     white: np.ndarray | None = None, dim: int = 2) -> tuple[np.ndarray, np.ndarray]:
+    n = L ** (dim - 1) * (L // 64)
+    b = np.empty(n, dtype=np.uint32) if black is None else black
+    w = np.empty(n, dtype=np.uint32) if white is None else white
     assert b.dtype == np.uint32 and w.dtype == np.uint32 and b.flags.c_contiguous and w.flags.c_contiguous
-    assert b.size == w.size == L * (L // 64)
+    assert b.size == w.size == n
     _check(lib().ising_get_planes(h, _ptr(b, ctypes.c_uint32), _ptr(w, ctypes.c_uint32)))
     return b, w
 
@@ -306,11 +322,14 @@ class Lattice:
         return ising_save(self.h)
 
     @classmethod
-    def load(cls, blob: bytes, stream=None) -> "Lattice":
+    def load(cls, blob: bytes, stream=None):
+        """A Lattice (or a Lattice3D for a 3D checkpoint) continuing the saved chain."""
         h = ising_load(blob, stream)
         import struct
         L, kernel, start = struct.unpack_from("<qqq", blob, 16)
         beta, seed = struct.unpack_from("<dQ", blob, 16 + 8 * 5)
+        if kernel == CUBIC:
+            return Lattice3D(L, beta, seed, start, _handle=h)
         return cls(L, beta, seed, start, kernel, _handle=h)
 
     def synchronize(self) -> None:
@@ -407,3 +426,20 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+class Lattice3D(Lattice):
+    """One cubic L x L x L lattice (an ``ising_t`` made by ``ising_init3d``)."""
+
+    def __init__(self, L: int, beta: float, seed: int, start: int = HOT, stream=None, _handle: int | None = None):
+        self.L, self.beta, self.seed, self.start, self.kernel = int(L), float(beta), int(seed), start, CUBIC
+        self.h = _handle if _handle is not None else ising_init3d(L, beta, seed, start, stream)
+
+    def get_lattice(self) -> np.ndarray:
+        return ising_get_lattice(self.h, self.L, dim=3)
+
+    def set_lattice(self, a: np.ndarray) -> None:
+        raise IsingError(ISING_EINVAL, "set_lattice is for 2D lattices; use set_planes")
+
+    def get_planes(self, black=None, white=None):
+        return ising_get_planes(self.h, self.L, black, white, dim=3)

@@ -43,6 +43,32 @@ def single_large() -> Lattice:
     return Lattice(L=65536, beta=BETA_TC, seed=2, start=HOT, sweeps=200)
 
 
+# Simple-cubic critical coupling from the Monte Carlo literature (Ferrenberg, Xu and
+# Landau 2018: 0.221654626), rounded; the 3D workloads run at it.
+BETA_C3 = 0.2216546
+
+
+def cubic_large() -> Lattice:
+    """3D single lattice: L = 2048 (2^33 sites, 1 GB of planes, larger than L2) at beta_c of
+    the cubic lattice, hot start from seed 3, 100 sweeps."""
+    return Lattice(L=2048, beta=BETA_C3, seed=3, start=HOT, sweeps=100)
+
+
+CUBIC_BINDER_LS = (64, 128, 256)
+CUBIC_BINDER_BETA_OVER_BC = (0.996, 0.998, 1.000, 1.002, 1.004)
+CUBIC_BINDER_SWEEPS = 100_000
+
+
+def cubic_binder_scan(sweeps: int = CUBIC_BINDER_SWEEPS) -> list[Lattice]:
+    """3D Binder-parameter scan: L = 64, 128, 256 at beta = beta_c * (0.996 ... 1.004),
+    cold start, seed 7,000,000 + 100 L + k; burn-in 10 %."""
+    out = []
+    for L in CUBIC_BINDER_LS:
+        for k, f in enumerate(CUBIC_BINDER_BETA_OVER_BC):
+            out.append(Lattice(L=L, beta=BETA_C3 * f, seed=7_000_000 + 100 * L + k, start=COLD, sweeps=sweeps))
+    return out
+
+
 def temperature_scan(n: int = 64, L: int = 1024) -> list[Lattice]:
     """n replicas of L = 1024, beta evenly spaced in [0.35, 0.55], cold start,
     seed_r = 3,000,000 + r; 5000 sweeps (a 100-sweep graph replayed 50 times),

@@ -87,6 +87,24 @@ def test_init_rejects_bad_start_and_kernel(lib):
         assert e.value.code == ising.ISING_EINVAL
 
 
+def test_thresholds3d_match_oracle(lib):
+    rng = np.random.default_rng(2)
+    for beta in np.concatenate([rng.uniform(0.0, 3.0, size=1000), [0.0, 0.2216546, 200.0]]):
+        T = ising.ising_thresholds3d(float(beta))
+        assert T == oracle.thresholds3d(float(beta)), beta
+        assert T[:2] == ising.ising_thresholds(float(beta))
+
+
+@pytest.mark.parametrize("L,start", [(0, ising.HOT), (96, ising.HOT), (32, ising.HOT), (16384, ising.HOT),
+                                     (64, 7)])
+def test_init3d_rejects_bad_arguments_before_device_work(lib, L, start):
+    with pytest.raises(ising.IsingError) as e:
+        ising.ising_init3d(L, 0.22, 1, start)
+    assert e.value.code == ising.ISING_EINVAL
+    with pytest.raises(ising.IsingError):
+        ising.ising_thresholds3d(float("nan"))
+
+
 def test_null_handles_are_rejected(lib):
     assert lib.ising_sweep(None, 1) == ising.ISING_EINVAL
     assert lib.ising_free(None) == ising.ISING_OK

@@ -6,7 +6,7 @@ independently written Philox4x32-10: with seed s it emits, for block b of four
 words, Philox(key = (s lo, s hi), counter = (b div 65536 as a 64-bit value in
 words 0-1, b mod 65536 in word 2, 0 in word 3)); an output offset of o words
 starts at block o/4.  This covers the key and counter words 0-2.  Counter word 3
-(the colour) is covered by the cuRAND device API in the GPU test file.
+is covered against cuRAND's device API in test_philox_curand_gpu.py.
 """
 import ctypes
 import ctypes.util
@@ -78,11 +78,17 @@ def test_philox_output_statistics():
 
 
 def test_site_word_keying():
-    """Site (i,j) of colour c uses word p & 3 of counter (p >> 2, 0, sweep, c)."""
-    L, seed = 64, 0xABCDEF0123
+    """Site (i,j) of colour c uses word p & 3 of counter (sweep, q lo, c, q hi), q = p >> 2."""
+    seed = 0xABCDEF0123
     key = (seed & 0xFFFFFFFF, seed >> 32)
-    for (i, j) in [(0, 0), (0, 1), (1, 0), (5, 37), (63, 63), (31, 6)]:
+    cases = [(64, i, j) for (i, j) in [(0, 0), (0, 1), (1, 0), (5, 37), (63, 63), (31, 6)]]
+    # L = 2^18: q passes 2^32 in the lower rows, so q's high word is non-zero
+    cases += [(1 << 18, 200000, 12345), (1 << 18, (1 << 18) - 1, (1 << 18) - 2)]
+    for (L, i, j) in cases:
         c = (i + j) & 1
         p = i * (L // 2) + (j >> 1)
+        q = p >> 2
         for sweep in (0, 7, 0xFFFFFFFF):
-            assert oracle.site_word(L, i, j, seed, sweep, c) == oracle.philox4x32_10((p >> 2, 0, sweep, c), key)[p & 3]
+            want = oracle.philox4x32_10((sweep, q & 0xFFFFFFFF, c, q >> 32), key)[p & 3]
+            assert oracle.site_word(L, i, j, seed, sweep, c) == want
+    assert (200000 * (1 << 17)) >> 2 >= 1 << 32
