@@ -31,21 +31,23 @@ sys.path.insert(0, ROOT)
 
 METRIC = "spin-flip attempts/ns on 1 GB300 (bit-packed checkerboard sweep, bit-exact)"
 UNIT = "flips/ns"
-# Algorithmic work per site update.  A Philox4x32-10 call serves 4 sites with 10
-# rounds of two 32x32->64 products and two three-input XORs.  The site index enters
-# through counter word 1, so the two round-1 products, round 2's B product and
-# round 3's A product do not depend on the site and are formed once per launch,
-# leaving 16 products + 18 XORs per call: 4 products and 4.5 XORs per site.  The
-# acceptance test adds 2 threshold compares per site and the neighbour count /
-# flip mask ~12 bitwise operations per 32 sites.
-MULS_PER_SITE_SWEEP = 4.0
-ALU_OPS_PER_SITE = 4.5 + 2.0 + 0.375
-# Integer multiply pipe: 16 lanes per scheduler, 4 schedulers per SM, a 32x32->64
-# product taking two lane-cycles -> 32 products per clock per SM.  Logic and
-# compare instructions run on the ALU pipe: 64 per clock per SM.
-MULS_PER_CLK_SM = 32.0
+# Roofline.  The sweep is integer work in registers (Philox4x32-10, a bitwise
+# neighbour count, bit-sliced threshold tests); memory moves 3/16 byte per site
+# update and does not bind.  With bit-sliced uniforms a plane word draws only the
+# Philox calls its sites need to be decided (about 2 of 8 on average, more where a
+# thread waits for its slowest word and a warp for its slowest thread), so the work
+# per site is data-dependent and is counted as executed instructions: ncu's
+# smsp__inst_executed.sum of one launch of the same kernel on the same workload,
+# committed under profiles/ with a hash of the kernel's sources, times 32 lanes.
+# The binding resource is instruction issue: one warp instruction per clock per
+# scheduler, 4 schedulers per SM -> 128 thread-instruction slots per clock per SM.
+ISSUE_SLOTS_PER_CLK_SM = 128.0
 ALU_OPS_PER_CLK_SM = 64.0
 N_SMS = 152
+KERNEL_SOURCES = {
+    "packed_half_sweep": ("sweep_packed.cu", "word_update.cuh", "philox.cuh", "ising_internal.cuh"),
+    "cubic_half_sweep": ("sweep3d.cu", "sweep3d.cuh", "word_update.cuh", "philox.cuh"),
+}
 # algorithmic bytes per site per sweep (packed): each half-sweep reads the target
 # and source planes and writes the target plane, N/2 bits each
 BYTES_PER_SITE_SWEEP = 3.0 * 2 * (0.5 / 8.0)
@@ -140,26 +142,50 @@ def measured_peaks() -> dict:
     return {}
 
 
-def kernel_source_hash() -> str:
+def kernel_source_hash(kernel: str = "packed_half_sweep") -> str:
     h = hashlib.sha256()
-    for f in ("sweep_packed.cu", "word_update.cuh", "philox.cuh", "ising_internal.cuh"):
+    for f in KERNEL_SOURCES[kernel]:
         with open(os.path.join(ROOT, "paper_1903_11714_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def committed_traffic(L: int):
-    """DRAM bytes per half-sweep launch from the committed ncu summary, if it was
-    taken on the current kernel source (else None)."""
-    p = os.path.join(ROOT, "profiles", "packed_half_sweep_traffic.json")
+def committed_counters(kernel: str):
+    """Per-site ncu counters of one launch of `kernel` (profiles/<kernel>_counters.json):
+    thread-instruction slots and DRAM bytes per updated site.  'current' is False when
+    the kernel's sources changed after the capture."""
+    p = os.path.join(ROOT, "profiles", f"{kernel}_counters.json")
     if not os.path.exists(p):
         return None
     with open(p) as f:
         d = json.load(f)
-    if d.get("kernel_source_hash") != kernel_source_hash():
-        return None
-    per_site = d.get("dram_bytes_per_site_per_launch")
-    return None if per_site is None else per_site * L * L
+    sites = d["sites_per_launch"]
+    return {"current": d.get("kernel_source_hash") == kernel_source_hash(kernel),
+            "inst_slots_per_site": 32.0 * d["warp_inst_per_launch"] / sites,
+            "dram_bytes_per_site": (d["dram_bytes_read_per_launch"] + d["dram_bytes_write_per_launch"]) / sites,
+            "capture": d.get("command")}
+
+
+def issue_roofline(kernel: str, sites_per_launch: float, t_launch_s: float, sm_max: float, peaks: dict) -> dict:
+    """Roofline of one half-sweep launch against the SM's instruction-issue rate."""
+    c = committed_counters(kernel)
+    peak = ISSUE_SLOTS_PER_CLK_SM * N_SMS * sm_max * 1e6 / 1e12
+    hbm_bytes = BYTES_PER_SITE_SWEEP * sites_per_launch
+    out = {"bound": "alu", "achieved": None, "peak": peak, "unit": "Tinst/s", "frac": None, "traffic": None,
+           "peak_basis": f"instruction issue: 4 schedulers x 32 lanes = {ISSUE_SLOTS_PER_CLK_SM:.0f} thread-instruction "
+                         f"slots/clk/SM x {N_SMS} SMs x {sm_max:.0f} MHz",
+           "hbm_achieved_gbs": hbm_bytes / t_launch_s / 1e9, "hbm_peak_gbs": peaks.get("hbm_gbs", 6800.0)}
+    if c is not None:
+        inst = c["inst_slots_per_site"] * sites_per_launch
+        out["achieved"] = inst / t_launch_s / 1e12
+        out["frac"] = out["achieved"] / peak
+        out["inst_slots_per_site"] = c["inst_slots_per_site"]
+        out["counters"] = "current" if c["current"] else "stale: kernel source changed after the capture"
+        if c["current"]:
+            out["traffic"] = c["dram_bytes_per_site"] * sites_per_launch
+        out["alu_view"] = {"peak_tops": ALU_OPS_PER_CLK_SM * N_SMS * sm_max * 1e6 / 1e12,
+                           "note": "ALU pipe (16 lanes x 4 schedulers); its busy share is in the profile summary"}
+    return out
 
 
 def cpu_baseline_sample(L: int, beta: float, seed: int, start: int) -> dict:
@@ -274,9 +300,8 @@ def run_batched(args, which: str) -> None:
     arena = sum(l.L * l.L // 8 + 16 * (l.sweeps + warm) + 4096 for l in lats)
     st = torch.cuda.Stream()
     tiles = {}
-    if which == "uneven":
-        for L in sorted({l.L for l in lats}):
-            tiles[L] = ising.ising_autotune(L)[0]
+    for L in sorted({l.L for l in lats}):
+        tiles[L] = ising.ising_autotune(L)[0]
     b = ising.Batch(len(lats), max_L, arena, 0, stream=st)
     for l in lats:
         b.add(l.L, l.beta, l.seed, l.start, l.sweeps + warm, tiles.get(l.L, 0))
@@ -350,9 +375,7 @@ def run_cubic(args) -> None:
     lat.close()
     value = steps * N / (ms * 1e6)
     t_launch_s = ms * 1e-3 / (2 * steps)
-    achieved = MULS_PER_SITE_SWEEP * N / 2 / t_launch_s / 1e12
-    peak = MULS_PER_CLK_SM * N_SMS * sm_max * 1e6 / 1e12
-    alu_ops = 4.5 + 3.0 + 0.6  # Philox XORs, three threshold compares, 6-input adder and flip
+    roofline = issue_roofline("cubic_half_sweep", N / 2, t_launch_s, sm_max, peaks)
     cpu = None
     if not args.no_cpu_baseline:
         cpu = cubic_cpu_baseline(cfg.beta, cfg.seed)
@@ -361,15 +384,7 @@ def run_cubic(args) -> None:
         "workload": "cubic", "unit": UNIT, "value": value, "steps": steps, "warmup": args.warmup,
         "ms_per_step": ms / steps, "higher_is_better": True,
         "config": {**cfg.as_dict(), "l2": "inputs larger than L2 (1 GB planes vs 129 MB L2), no flush"},
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tmul/s", "frac": achieved / peak,
-                     "traffic": None,
-                     "peak_basis": f"integer multiply pipe, {MULS_PER_CLK_SM:.0f} products/clk/SM x {N_SMS} SMs x "
-                                   f"{sm_max:.0f} MHz; {MULS_PER_SITE_SWEEP} Philox products per site update",
-                     "alu_view": {"achieved_tops": alu_ops * N / 2 / t_launch_s / 1e12,
-                                  "peak_tops": ALU_OPS_PER_CLK_SM * N_SMS * sm_max * 1e6 / 1e12,
-                                  "ops_per_site": alu_ops},
-                     "hbm_achieved_gbs": BYTES_PER_SITE_SWEEP * N / 2 / t_launch_s / 1e9,
-                     "hbm_peak_gbs": peaks.get("hbm_gbs", 6800.0)},
+        "roofline": roofline,
         "cpu_baseline": cpu, "gpu_launches": 2 * steps, "clocks": clocks}))
 
 
@@ -593,23 +608,14 @@ def main() -> None:
     # dominant kernel: the packed half-sweep (2 launches per sweep + 1 counter advance per call)
     launches = 2 * args.steps + 1
     t_launch_s = ms * 1e-3 / (2 * args.steps)
-    muls_per_launch = MULS_PER_SITE_SWEEP * N / 2
-    achieved = muls_per_launch / t_launch_s / 1e12
-    peak = MULS_PER_CLK_SM * N_SMS * sm_max * 1e6 / 1e12
-    alu_achieved = ALU_OPS_PER_SITE * N / 2 / t_launch_s / 1e12
-    bytes_per_launch = BYTES_PER_SITE_SWEEP * N / 2 if kernel == ising.PACKED else 2.0 * N
-    traffic = committed_traffic(L) if kernel == ising.PACKED else None
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tmul/s", "frac": achieved / peak,
-                "traffic": traffic,
-                "peak_basis": f"integer multiply pipe: {MULS_PER_CLK_SM:.0f} 32x32->64 products/clk/SM (16 lanes x 4 "
-                              f"schedulers, 2 lane-cycles each) x {N_SMS} SMs x {sm_max:.0f} MHz; achieved counts "
-                              f"{MULS_PER_SITE_SWEEP} Philox products per site update",
-                "probe_mul_xor_steps_per_clk_sm": mul_per_clk, "probe_alu_ops_per_clk_sm": alu_per_clk,
-                "alu_view": {"achieved_tops": alu_achieved,
-                             "peak_tops": ALU_OPS_PER_CLK_SM * N_SMS * sm_max * 1e6 / 1e12,
-                             "ops_per_site": ALU_OPS_PER_SITE},
-                "hbm_achieved_gbs": bytes_per_launch / t_launch_s / 1e9,
-                "hbm_peak_gbs": peaks.get("hbm_gbs", 6800.0)}
+    if kernel == ising.PACKED:
+        roofline = issue_roofline("packed_half_sweep", N / 2, t_launch_s, sm_max, peaks)
+    else:
+        roofline = {"bound": "alu", "achieved": None, "peak": None, "unit": "Tinst/s", "frac": None, "traffic": None,
+                    "hbm_achieved_gbs": 2.0 * N / t_launch_s / 1e9, "hbm_peak_gbs": peaks.get("hbm_gbs", 6800.0),
+                    "note": "plain int8 kernel: no committed counters"}
+    roofline["probe_alu_ops_per_clk_sm"] = alu_per_clk
+    roofline["probe_mul_xor_steps_per_clk_sm"] = mul_per_clk
 
     e2e = None
     if not args.no_e2e and kernel == ising.PACKED and rank == 0:

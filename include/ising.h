@@ -12,12 +12,15 @@
  *
  * Determinism.  The chain is a pure function of (L, beta, seed, start state,
  * sweep count):
- *   - uniform draw of site (i,j) of colour c in sweep s: output word (p & 3) of
- *     Philox4x32-10 (Salmon et al., SC'11) with key (seed lo32, seed hi32) and
- *     counter (s, q lo32, c, q hi32), where p = i*(L/2) + (j>>1), q = p >> 2;
- *   - flip iff h <= 0, or word < T_h with T_h = min(2^32, ceil(exp(-2 beta h) 2^32))
+ *   - uniform of site (i,j) of colour c in sweep s: with plane index
+ *     p = i*(L/2) + (j>>1), plane word g = p >> 5 and bit b = p & 31,
+ *     U = sum_k bit_b(R_k) 2^(31-k), where R_k (k = 0..31) is output word (k & 3)
+ *     of Philox4x32-10 (Salmon et al., SC'11) with key (seed lo32, seed hi32) and
+ *     counter (s, q lo32, c, q hi32), q = 8g + (k >> 2): the 32 random words of a
+ *     plane word are the bit planes of its 32 uniforms, R_0 the top one;
+ *   - flip iff h <= 0, or U < T_h with T_h = min(2^32, ceil(exp(-2 beta h) 2^32))
  *     computed on the host in FP64 (see ising_thresholds);
- *   - hot start: sigma = +1 iff the word drawn with s = 0xFFFFFFFF is < 2^31;
+ *   - hot start: sigma = +1 iff the uniform drawn with s = 0xFFFFFFFF is < 2^31;
  *     cold start: all +1.
  *   Both kernels (bit-packed and int8) produce the same lattice bit for bit.
  *
@@ -70,7 +73,7 @@ const char *ising_version(void);
  * Acceptance thresholds (Sec. 3.1 acceptance rule, Algorithm 1-2's
  * exp(-2 nn sigma) with beta restored): T[0] for h = 2, T[1] for h = 4,
  * T_h = min(2^32, ceil(exp(-2 beta h) * 2^32)) in FP64 with the host libm exp.
- * A uniform 32-bit word x accepts iff x < T_h.  beta must be finite and >= 0.
+ * A site's 32-bit uniform U accepts iff U < T_h.  beta must be finite and >= 0.
  * Host-only; needs no GPU.  Errors: EINVAL.
  */
 int ising_thresholds(double beta, uint64_t T[2]);
@@ -165,11 +168,10 @@ int ising_free(ising_t h);
  * checkerboard algorithm carries over to three dimensions; these handles run
  * that generalisation on the cubic L x L x L torus: colour c = (i+j+k) & 1
  * (black first), nn = sum of the six neighbours, h = sigma * nn, flip iff
- * h <= 0 or the site's uniform word is below T_h, h = 2, 4, 6.  E = H(sigma)
- * over the 3N bonds.  Uniform of site (i,j,k): output word (p & 3) of
- * Philox4x32-10 with key (seed lo32, seed hi32) and counter
- * (s, q lo32, c, q hi32), p = (i*L + j)*(L/2) + (k>>1), q = p >> 2 -- the 2D
- * keying with row index i*L + j.  Hot start as in 2D.
+ * h <= 0 or the site's uniform is below T_h, h = 2, 4, 6.  E = H(sigma)
+ * over the 3N bonds.  Uniform of site (i,j,k): as in 2D from plane index
+ * p = (i*L + j)*(L/2) + (k>>1) -- the 2D keying with row index i*L + j.  Hot
+ * start as in 2D.
  * ---------------------------------------------------------------------- */
 
 /*

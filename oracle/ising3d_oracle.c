@@ -22,10 +22,10 @@
  *
  * Readings (the paper gives no 3D algorithm; these mirror the 2D readings):
  *   - Site (i,j,k) has colour-plane index p = (i*Y + j)*(Z/2) + (k>>1): the 2D
- *     index with the row (i,j) numbered i*Y + j.  Its uniform is output word
- *     (p & 3) of Philox4x32-10 with key (seed low, seed high) and counter
- *     (sweep, q low 32, c, q high 32), q = p >> 2 -- the 2D layout.
- *   - Hot start: sigma = +1 iff the word drawn with sweep = 0xFFFFFFFF is below
+ *     index with the row (i,j) numbered i*Y + j.  Its uniform is drawn from p as
+ *     in 2D: U = sum_k bit_{p & 31}(R_k) 2^(31-k) with R_0 .. R_31 the random words
+ *     of plane word p >> 5 (oracle_word_randoms of ising_oracle.c).
+ *   - Hot start: sigma = +1 iff the uniform drawn with sweep = 0xFFFFFFFF is below
  *     2^31; cold start all +1.
  *   - M = sum sigma; E = H = -sum over the 3N bonds.  A dimension of extent 2
  *     makes the two neighbours along it the same site, counted twice in nn and
@@ -43,8 +43,8 @@
 
 #define ORACLE_API __attribute__((visibility("default")))
 
-/* Philox4x32-10 of ising_oracle.c (same shared object). */
-void oracle_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+/* The random words of one plane word, from ising_oracle.c (same shared object). */
+void oracle_word_randoms(uint64_t g, uint64_t seed, uint32_t sweep, int c, uint32_t R[32]);
 
 static inline int64_t wrap3(int64_t a, int64_t n)
 {
@@ -71,17 +71,38 @@ ORACLE_API int oracle3d_accept(int h, uint32_t x, const uint64_t T[3])
     return (uint64_t)x < T[h / 2 - 1];
 }
 
+static uint32_t uniform3_of(const uint32_t R[32], int b)
+{
+    uint32_t u = 0;
+    for (int k = 0; k < 32; ++k) u |= ((R[k] >> b) & 1u) << (31 - k);
+    return u;
+}
+
+struct word_cache3 {
+    uint64_t g;
+    uint32_t R[32];
+};
+
+static uint32_t cached_uniform3(struct word_cache3 *wc, uint64_t p, uint64_t seed, uint32_t sweep, int c)
+{
+    if ((p >> 5) != wc->g) {
+        wc->g = p >> 5;
+        oracle_word_randoms(wc->g, seed, sweep, c, wc->R);
+    }
+    return uniform3_of(wc->R, (int)(p & 31));
+}
+
+static uint64_t plane_index3(int64_t Y, int64_t Z, int64_t i, int64_t j, int64_t k)
+{
+    return ((uint64_t)i * (uint64_t)Y + (uint64_t)j) * (uint64_t)(Z / 2) + (uint64_t)(k >> 1);
+}
+
 ORACLE_API uint32_t oracle3d_site_word(int64_t X, int64_t Y, int64_t Z, int64_t i, int64_t j, int64_t k,
                                        uint64_t seed, uint32_t sweep, int c)
 {
     (void)X;
-    uint64_t p = ((uint64_t)i * (uint64_t)Y + (uint64_t)j) * (uint64_t)(Z / 2) + (uint64_t)(k >> 1);
-    uint64_t q = p >> 2;
-    uint32_t ctr[4] = {sweep, (uint32_t)q, (uint32_t)c, (uint32_t)(q >> 32)};
-    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
-    uint32_t out[4];
-    oracle_philox4x32_10(ctr, key, out);
-    return out[p & 3];
+    struct word_cache3 wc = {UINT64_MAX, {0}};
+    return cached_uniform3(&wc, plane_index3(Y, Z, i, j, k), seed, sweep, c);
 }
 
 #define AT(s, i, j, k) (s)[((i) * Y + (j)) * Z + (k)]
@@ -91,15 +112,18 @@ ORACLE_API void oracle3d_init(int8_t *s, int64_t X, int64_t Y, int64_t Z, uint64
 {
 #pragma omp parallel for schedule(static) if (X * Y * Z >= 32768)
     for (int64_t i = 0; i < X; ++i)
-        for (int64_t j = 0; j < Y; ++j)
+        for (int64_t j = 0; j < Y; ++j) {
+            struct word_cache3 wc[2] = {{UINT64_MAX, {0}}, {UINT64_MAX, {0}}};
             for (int64_t k = 0; k < Z; ++k) {
                 if (start == 1) {
                     AT(s, i, j, k) = 1;
                 } else {
-                    uint32_t x = oracle3d_site_word(X, Y, Z, i, j, k, seed, 0xFFFFFFFFu, (int)((i + j + k) & 1));
+                    int c = (int)((i + j + k) & 1);
+                    uint32_t x = cached_uniform3(&wc[c], plane_index3(Y, Z, i, j, k), seed, 0xFFFFFFFFu, c);
                     AT(s, i, j, k) = (x < 0x80000000u) ? 1 : -1;
                 }
             }
+        }
 }
 
 /* M = sum sigma, E = -sum over the 3N torus bonds. */
@@ -127,7 +151,8 @@ static int64_t half_sweep3d(int8_t *s, int64_t X, int64_t Y, int64_t Z, int c, c
     int64_t dE = 0;
 #pragma omp parallel for reduction(+ : dE) schedule(static) if (X * Y * Z >= 32768)
     for (int64_t i = 0; i < X; ++i)
-        for (int64_t j = 0; j < Y; ++j)
+        for (int64_t j = 0; j < Y; ++j) {
+            struct word_cache3 wc = {UINT64_MAX, {0}};
             for (int64_t k = 0; k < Z; ++k) {
                 if (((i + j + k) & 1) != c) continue;
                 int nn = AT(s, wrap3(i - 1, X), j, k) + AT(s, wrap3(i + 1, X), j, k)
@@ -135,12 +160,13 @@ static int64_t half_sweep3d(int8_t *s, int64_t X, int64_t Y, int64_t Z, int c, c
                        + AT(s, i, j, wrap3(k - 1, Z)) + AT(s, i, j, wrap3(k + 1, Z));
                 int h = AT(s, i, j, k) * nn;
                 uint32_t x = words ? words[(i * Y + j) * Z + k]
-                                   : oracle3d_site_word(X, Y, Z, i, j, k, seed, sweep, c);
+                                   : cached_uniform3(&wc, plane_index3(Y, Z, i, j, k), seed, sweep, c);
                 if (oracle3d_accept(h, x, T)) {
                     AT(s, i, j, k) = (int8_t)(-AT(s, i, j, k));
                     dE += 2 * h;
                 }
             }
+        }
     return dE;
 }
 

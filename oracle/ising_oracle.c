@@ -22,10 +22,17 @@
  *     Dror, Shaw, "Parallel random numbers: as easy as 1, 2, 3", SC'11); the
  *     test u < p with u = x / 2^32 becomes x < T_h, T_h = min(2^32, ceil(p 2^32)),
  *     p = exp(-2 beta h) evaluated in FP64 by the host libm.  h <= 0 always flips.
- *   - Site (i,j) of colour c has colour-plane index p = i*(L/2) + (j>>1).  Its
- *     word is output word (p & 3) of Philox with key = (seed low 32, seed high 32)
- *     and counter = (sweep, q low 32, c, q high 32), q = p >> 2.
- *   - Hot start: sigma = +1 iff the Philox word drawn with sweep = 0xFFFFFFFF is
+ *   - Site (i,j) of colour c has colour-plane index p = i*(L/2) + (j>>1); the
+ *     plane indices 32g .. 32g+31 form plane word g = p >> 5, and b = p & 31 is
+ *     the site's bit position in it.  Word g draws 32 random words R_0 .. R_31 per
+ *     sweep: R_k is output word (k & 3) of Philox with key = (seed low 32, seed
+ *     high 32) and counter = (sweep, q low 32, c, q high 32), q = 8g + (k >> 2).
+ *     The site's uniform is U = sum_k bit_b(R_k) 2^(31-k): R_0 holds the top bit
+ *     of the uniforms of all 32 sites of the word, R_31 the bottom bit.  (Every
+ *     bit of U is an independent fair bit, as with a whole 32-bit draw; this
+ *     assignment lets a word-parallel comparison stop at the first bits that
+ *     decide it.)
+ *   - Hot start: sigma = +1 iff the uniform drawn with sweep = 0xFFFFFFFF is
  *     below 2^31.  Cold start: all +1.
  *   - M = sum sigma; E = -sum_{i,j} sigma[i][j] (sigma[i+1][j] + sigma[i][j+1]),
  *     i.e. H with mu = 0, J = 1 over the 2N torus bonds.
@@ -105,16 +112,50 @@ static inline int64_t wrap(int64_t a, int64_t L)
     return a < 0 ? a + L : a;
 }
 
-/* Uniform word of site (i,j) of colour c for the given sweep (see header). */
+/* The 32 random words R_0 .. R_31 of plane word g for one sweep and colour (see header). */
+ORACLE_API void oracle_word_randoms(uint64_t g, uint64_t seed, uint32_t sweep, int c, uint32_t R[32])
+{
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    for (int n = 0; n < 8; ++n) {
+        uint64_t q = 8 * g + (uint64_t)n;
+        uint32_t ctr[4] = {sweep, (uint32_t)q, (uint32_t)c, (uint32_t)(q >> 32)};
+        oracle_philox4x32_10(ctr, key, R + 4 * n);
+    }
+}
+
+/* U of bit position b: bit b of R_k is the bit of weight 2^(31-k). */
+static uint32_t uniform_of(const uint32_t R[32], int b)
+{
+    uint32_t u = 0;
+    for (int k = 0; k < 32; ++k) u |= ((R[k] >> b) & 1u) << (31 - k);
+    return u;
+}
+
+/* Uniforms of one row, colour c only, through a cache of the current plane word's
+ * random words (a row of colour c holds whole plane words when L % 64 == 0 and
+ * parts of two otherwise; the cache follows g either way). */
+struct word_cache {
+    uint64_t g;
+    uint32_t R[32];
+};
+
+static uint32_t cached_uniform(struct word_cache *wc, uint64_t p, uint64_t seed, uint32_t sweep, int c)
+{
+    uint64_t g = p >> 5;
+    if (g != wc->g) {
+        oracle_word_randoms(g, seed, sweep, c, wc->R);
+        wc->g = g;
+    }
+    return uniform_of(wc->R, (int)(p & 31));
+}
+
+/* Uniform of site (i,j) of colour c for the given sweep (see header). */
 static uint32_t site_word(int64_t L, int64_t i, int64_t j, uint64_t seed, uint32_t sweep, int c)
 {
     uint64_t p = (uint64_t)i * (uint64_t)(L / 2) + (uint64_t)(j >> 1);
-    uint64_t q = p >> 2;
-    uint32_t ctr[4] = {sweep, (uint32_t)q, (uint32_t)c, (uint32_t)(q >> 32)};
-    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
-    uint32_t out[4];
-    oracle_philox4x32_10(ctr, key, out);
-    return out[p & 3];
+    uint32_t R[32];
+    oracle_word_randoms(p >> 5, seed, sweep, c, R);
+    return uniform_of(R, (int)(p & 31));
 }
 
 ORACLE_API uint32_t oracle_site_word(int64_t L, int64_t i, int64_t j, uint64_t seed, uint32_t sweep, int c)
@@ -126,15 +167,19 @@ ORACLE_API uint32_t oracle_site_word(int64_t L, int64_t i, int64_t j, uint64_t s
 ORACLE_API void oracle_init(int8_t *s, int64_t L, uint64_t seed, int start)
 {
 #pragma omp parallel for schedule(static) if (L >= 64)
-    for (int64_t i = 0; i < L; ++i)
+    for (int64_t i = 0; i < L; ++i) {
+        struct word_cache wc[2] = {{UINT64_MAX, {0}}, {UINT64_MAX, {0}}};
         for (int64_t j = 0; j < L; ++j) {
             if (start == 1) {
                 s[i * L + j] = 1;
             } else {
-                uint32_t x = site_word(L, i, j, seed, 0xFFFFFFFFu, (int)((i + j) & 1));
+                int c = (int)((i + j) & 1);
+                uint64_t p = (uint64_t)i * (uint64_t)(L / 2) + (uint64_t)(j >> 1);
+                uint32_t x = cached_uniform(&wc[c], p, seed, 0xFFFFFFFFu, c);
                 s[i * L + j] = (x < 0x80000000u) ? 1 : -1;
             }
         }
+    }
 }
 
 /* M = sum sigma, E = -sum over the 2N torus bonds (H of Sec. 3, mu = 0, J = 1). */
@@ -162,9 +207,8 @@ static int64_t half_sweep(int8_t *s, int64_t L, int c, uint64_t T2, uint64_t T4,
     int64_t dE = 0;
 #pragma omp parallel for reduction(+ : dE) schedule(static) if (L >= 64)
     for (int64_t i = 0; i < L; ++i) {
-        /* Four same-colour neighbours along a row share one Philox call; cache it. */
-        uint64_t cached_q = UINT64_MAX;
-        uint32_t cached[4] = {0, 0, 0, 0};
+        /* The 32 same-colour sites of a plane word share its 32 random words; cache them. */
+        struct word_cache wc = {UINT64_MAX, {0}};
         for (int64_t j = 0; j < L; ++j) {
             if (((i + j) & 1) != c) continue;
             int nn = s[wrap(i - 1, L) * L + j] + s[wrap(i + 1, L) * L + j]
@@ -175,14 +219,7 @@ static int64_t half_sweep(int8_t *s, int64_t L, int c, uint64_t T2, uint64_t T4,
                 x = words[i * L + j];
             } else {
                 uint64_t p = (uint64_t)i * (uint64_t)(L / 2) + (uint64_t)(j >> 1);
-                uint64_t q = p >> 2;
-                if (q != cached_q) {
-                    uint32_t ctr[4] = {sweep, (uint32_t)q, (uint32_t)c, (uint32_t)(q >> 32)};
-                    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
-                    oracle_philox4x32_10(ctr, key, cached);
-                    cached_q = q;
-                }
-                x = cached[p & 3];
+                x = cached_uniform(&wc, p, seed, sweep, c);
             }
             if (oracle_accept(h, x, T2, T4)) {
                 s[i * L + j] = (int8_t)(-s[i * L + j]);
@@ -252,30 +289,37 @@ ORACLE_API int oracle_window(int64_t L, double beta, uint64_t seed, int start, i
     if (!buf) return -1;
     /* Start state at global coordinates. */
 #pragma omp parallel for schedule(static) if (L >= 64)
-    for (int64_t a = 0; a < H; ++a)
+    for (int64_t a = 0; a < H; ++a) {
+        struct word_cache wc[2] = {{UINT64_MAX, {0}}, {UINT64_MAX, {0}}};
         for (int64_t b = 0; b < W; ++b) {
             int64_t gi = wrap(i0 - R + a, L), gj = wrap(j0 - R + b, L);
             if (start == 1) {
                 buf[a * W + b] = 1;
             } else {
-                uint32_t x = site_word(L, gi, gj, seed, 0xFFFFFFFFu, (int)((gi + gj) & 1));
+                int cc = (int)((gi + gj) & 1);
+                uint64_t p = (uint64_t)gi * (uint64_t)(L / 2) + (uint64_t)(gj >> 1);
+                uint32_t x = cached_uniform(&wc[cc], p, seed, 0xFFFFFFFFu, cc);
                 buf[a * W + b] = (x < 0x80000000u) ? 1 : -1;
             }
         }
+    }
     for (int64_t t = 0; t < 2 * nsweeps; ++t) {
         uint32_t sweep = (uint32_t)(sweep0 + t / 2);
         int c = (int)(t & 1);
         int64_t lo = t + 1, hi_a = H - t - 1, hi_b = W - t - 1;
 #pragma omp parallel for schedule(static) if (L >= 64)
-        for (int64_t a = lo; a < hi_a; ++a)
+        for (int64_t a = lo; a < hi_a; ++a) {
+            struct word_cache wc = {UINT64_MAX, {0}};
             for (int64_t b = lo; b < hi_b; ++b) {
                 int64_t gi = wrap(i0 - R + a, L), gj = wrap(j0 - R + b, L);
                 if (((gi + gj) & 1) != c) continue;
                 int nn = buf[(a - 1) * W + b] + buf[(a + 1) * W + b] + buf[a * W + b - 1] + buf[a * W + b + 1];
                 int hh = buf[a * W + b] * nn;
-                uint32_t x = site_word(L, gi, gj, seed, sweep, c);
+                uint64_t p = (uint64_t)gi * (uint64_t)(L / 2) + (uint64_t)(gj >> 1);
+                uint32_t x = cached_uniform(&wc, p, seed, sweep, c);
                 if (oracle_accept(hh, x, T[0], T[1])) buf[a * W + b] = (int8_t)(-buf[a * W + b]);
             }
+        }
     }
     for (int64_t a = 0; a < h; ++a)
         memcpy(out + a * w, buf + (a + R) * W + R, (size_t)w);
@@ -295,11 +339,14 @@ ORACLE_API void oracle_init_rows(int8_t *s, int64_t L, uint64_t seed, int start,
 #pragma omp parallel for schedule(static)
     for (int64_t a = 0; a < nrows; ++a) {
         int64_t i = wrap(row0 + a, L);
+        struct word_cache wc[2] = {{UINT64_MAX, {0}}, {UINT64_MAX, {0}}};
         for (int64_t j = 0; j < L; ++j) {
             if (start == 1) {
                 s[i * L + j] = 1;
             } else {
-                uint32_t x = site_word(L, i, j, seed, 0xFFFFFFFFu, (int)((i + j) & 1));
+                int c = (int)((i + j) & 1);
+                uint64_t p = (uint64_t)i * (uint64_t)(L / 2) + (uint64_t)(j >> 1);
+                uint32_t x = cached_uniform(&wc[c], p, seed, 0xFFFFFFFFu, c);
                 s[i * L + j] = (x < 0x80000000u) ? 1 : -1;
             }
         }
@@ -315,22 +362,14 @@ ORACLE_API int64_t oracle_half_sweep_rows(int8_t *s, int64_t L, int c, double be
 #pragma omp parallel for reduction(+ : dE) schedule(static)
     for (int64_t a = 0; a < nrows; ++a) {
         int64_t i = wrap(row0 + a, L);
-        uint64_t cached_q = UINT64_MAX;
-        uint32_t cached[4] = {0, 0, 0, 0};
+        struct word_cache wc = {UINT64_MAX, {0}};
         for (int64_t j = 0; j < L; ++j) {
             if (((i + j) & 1) != c) continue;
             int nn = s[wrap(i - 1, L) * L + j] + s[wrap(i + 1, L) * L + j]
                    + s[i * L + wrap(j - 1, L)] + s[i * L + wrap(j + 1, L)];
             int h = s[i * L + j] * nn;
             uint64_t p = (uint64_t)i * (uint64_t)(L / 2) + (uint64_t)(j >> 1);
-            uint64_t q = p >> 2;
-            if (q != cached_q) {
-                uint32_t ctr[4] = {sweep, (uint32_t)q, (uint32_t)c, (uint32_t)(q >> 32)};
-                uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
-                oracle_philox4x32_10(ctr, key, cached);
-                cached_q = q;
-            }
-            if (oracle_accept(h, cached[p & 3], T[0], T[1])) {
+            if (oracle_accept(h, cached_uniform(&wc, p, seed, sweep, c), T[0], T[1])) {
                 s[i * L + j] = (int8_t)(-s[i * L + j]);
                 dE += 2 * h;
             }

@@ -90,11 +90,8 @@ int64_t stage_bytes_for(int64_t L, int tile_rows)
 
 // Tile heights: powers of two from 4 to 256 rows; 2 rows only when a row is a
 // whole number of 16-byte units (W % 4 == 0), so that every bulk copy stays
-// 16-byte aligned.  The built-in choice stops at 64 rows: taller tiles pay only
-// when the tuner finds they do, since a batch of mid-size lattices cut into
-// 256-row tiles can hold fewer tiles than the persistent grid has CTAs.
+// 16-byte aligned.
 constexpr int kMaxTileRows = 256;
-constexpr int kDefaultMaxTileRows = 64;
 
 bool tile_rows_ok(int64_t L, int tr)
 {
@@ -103,22 +100,25 @@ bool tile_rows_ok(int64_t L, int tr)
            stage_bytes_for(L, tr) <= kStageCapBytes;
 }
 
-// Built-in tile height: about ISING_TILE_WORDS words per tile, clamped to [2, 64].
+// Built-in tile height: about ISING_TILE_WORDS words per tile and at most 64 rows.
+// Taller tiles (up to 256 rows) suit big batches and are what ising_autotune picks
+// for them, but a batch of a few small lattices cut that way holds fewer tiles than
+// the persistent grid has CTAs, so the built-in choice stays short.
 #ifndef ISING_TILE_WORDS
 #define ISING_TILE_WORDS 4096
 #endif
 int default_tile_rows(int64_t L)
 {
     const int64_t W = L / 64;
-    int tr = kDefaultMaxTileRows;
+    int tr = 64;
     while (tr > 2 && ((int64_t)tr * W > ISING_TILE_WORDS || !tile_rows_ok(L, tr))) tr >>= 1;
     if (!tile_rows_ok(L, tr)) tr = 4;
     return tr;
 }
 
-// Tile height for a lattice swept on its own: as for a batch, but small lattices
-// are cut into enough tiles to spread over the persistent grid (about two CTAs
-// per SM) instead of a few large ones.
+// Tile height for a lattice swept on its own (the single-lattice instance, two
+// CTAs per SM): the built-in height, lowered so that small lattices are cut into
+// enough tiles to spread over the persistent grid instead of a few large ones.
 int single_tile_rows(int64_t L)
 {
     const int grid = 2 * sm_count();
@@ -148,9 +148,11 @@ struct Engine {
     // handle keeps equal to the device's; plain launches then pass it by value
     const LatticeDesc* one = nullptr;
     bool capturing = false;
+    bool one_lattice = false;  // launches the single-lattice instance (sizes the grid by its occupancy)
 
-    int setup(int max_count_, int stage_bytes_, int threads_, cudaStream_t s)
+    int setup(int max_count_, int stage_bytes_, int threads_, cudaStream_t s, bool one_lattice_ = false)
     {
+        one_lattice = one_lattice_;
         max_count = max_count_;
         stage_bytes = (stage_bytes_ + 15) / 16 * 16;
         threads = threads_;
@@ -171,7 +173,7 @@ struct Engine {
         const size_t smem = (size_t)packed_smem_header_bytes(threads) + 2 * (size_t)stage_bytes;
         CK(packed_set_smem_limit(threads, smem));
         int per_sm = 0;
-        CK(packed_occupancy(threads, smem, &per_sm));
+        CK(packed_occupancy(threads, smem, &per_sm, one_lattice));
         if (per_sm < 1) return fail(ISING_EINVAL, "sweep kernel does not fit: %d threads, %zu B smem", threads, smem);
         grid = per_sm * sm_count();
         drop_graph();
@@ -636,7 +638,7 @@ int ising_init_ex(ising_t* out, int64_t L, double beta, uint64_t seed, int start
         d.sweep = 0;
         d.target = kNoTarget;
         d.active = 1;
-        rc = h->eng.setup(1, (int)stage_bytes_for(L, tr), 256, h->stream);
+        rc = h->eng.setup(1, (int)stage_bytes_for(L, tr), 256, h->stream, true);
         if (rc) {
             destroy_handle(h);
             return rc;

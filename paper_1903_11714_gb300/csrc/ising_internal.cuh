@@ -94,6 +94,8 @@ void set_last_error(const char* msg);
 // Packed sweep kernel configuration helpers (sweep_packed.cu).
 int packed_smem_header_bytes(int threads);
 cudaError_t packed_set_smem_limit(int threads, size_t bytes);
-cudaError_t packed_occupancy(int threads, size_t smem, int* blocks_per_sm);
+// Resident CTAs per SM of the sweep kernel: the single-lattice instance (one) or
+// the general one, which the two launch bounds give different register budgets.
+cudaError_t packed_occupancy(int threads, size_t smem, int* blocks_per_sm, bool one = false);
 
 }  // namespace ising

@@ -12,7 +12,6 @@
 namespace ising {
 namespace {
 
-constexpr uint32_t kInitSweep = 0xFFFFFFFFu;
 
 __global__ void packed_init_kernel(uint32_t* black, uint32_t* white, int64_t L, uint64_t key, int start)
 {
@@ -27,18 +26,8 @@ __global__ void packed_init_kernel(uint32_t* black, uint32_t* white, int64_t L, 
             plane[idx] = 0xFFFFFFFFu;
             continue;
         }
-        const int64_t i = idx / W, w = idx - i * W;
-        const uint64_t q0 = (uint64_t)i * (uint64_t)(L / 8) + 8ull * (uint64_t)w;
-        uint32_t bits = 0;
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const uint64_t q = q0 + j;
-            uint32_t x[4];
-            site_philox(q, kInitSweep, (uint32_t)c, key, x);
-#pragma unroll
-            for (int m = 0; m < 4; ++m) bits |= (x[m] < 0x80000000u ? 1u : 0u) << (4 * j + m);
-        }
-        plane[idx] = bits;
+        // plane word idx = i * W + w holds plane indices 32 idx .. 32 idx + 31
+        plane[idx] = hot_start_word((uint64_t)idx, (uint32_t)c, key);
     }
 }
 

@@ -2,8 +2,13 @@
 // numbers: as easy as 1, 2, 3", SC'11), specialised to the counter layout of the
 // sweep: counter = (sweep, q low 32, colour, q high 32), key = (seed low, seed high).
 //
-// The draw replaces the paper's random_uniform (Algorithms 1-2): the uniform of a
-// site of colour-plane index p is output word (p & 3) of the call with q = p >> 2.
+// The draw replaces the paper's random_uniform (Algorithms 1-2).  The colour-plane
+// indices 32g .. 32g+31 form plane word g (one 32-bit word of a bit plane); the
+// word's 32 random words R_0 .. R_31 are the outputs of the eight calls
+// q = 8g .. 8g+7 (R_k = output k & 3 of call q = 8g + k/4), and the uniform of the
+// site at bit b is U = sum_k bit_b(R_k) 2^(31-k).  So R_k is bit plane 31 - k of
+// the 32 uniforms of the word: a word-parallel comparison U < T can read R_0, R_1,
+// ... and stop as soon as every site is decided, leaving later calls undrawn.
 //
 // One Philox round maps (x0,x1,x2,x3) under round key (k0,k1) to
 //   (hi(B*x2) ^ x1 ^ k0, lo(B*x2), hi(A*x0) ^ x3 ^ k1, lo(A*x0)),
@@ -69,52 +74,52 @@ __device__ __forceinline__ PhiloxWordConsts philox_consts(uint64_t key, uint32_t
     return c;
 }
 
-// The eight calls of one 32-site word, q_lo .. q_lo + 7 with q_lo % 8 == 0 (a word
-// starts at a multiple of 32 sites, so q_lo + j = q_lo ^ j), advanced round by
-// round together so the multiplies of different calls overlap, with each round key
-// formed once per round for all eight.  out[4 j + m] is output word m of call j,
-// i.e. the draw of the word's site 4 j + m.
-__device__ __forceinline__ void philox_word8(uint32_t q_lo, const PhiloxWordConsts& c, uint64_t key,
-                                             uint32_t out[32])
+// Call c (0..7) of G plane words at once: word k's call is q = q_lo[k] + c with
+// q_lo[k] % 8 == 0 (so q_lo + c = q_lo ^ c), passed as base[k] = q_lo[k] ^ x0k.
+// The G calls advance round by round together so that their multiplies overlap,
+// with each round key formed once per round.  o[k][m] = output word m of word k's
+// call, i.e. the random word R_{4c+m} of that plane word.
+template <int G>
+__device__ __forceinline__ void philox_calls(const uint32_t base[G], uint32_t c, const PhiloxWordConsts& pc,
+                                             uint64_t key, uint32_t o[G][4])
 {
     const uint32_t k0 = (uint32_t)key, k1 = (uint32_t)(key >> 32);
-    const uint32_t base = q_lo ^ c.x0k;
-    uint32_t y0[8], y1[8], y2[8], y3[8];
+    uint32_t y0[G], y1[G], y2[G], y3[G];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
+    for (int k = 0; k < G; ++k) {
         uint32_t hi, lo;
-        mulhilo(kPhiloxA, base ^ (uint32_t)j, hi, lo);  // round 2, the varying product
-        const uint32_t r2_y2 = hi ^ c.y2k;
+        mulhilo(kPhiloxA, base[k] ^ c, hi, lo);  // round 2, the varying product
+        const uint32_t r2_y2 = hi ^ pc.y2k;
         const uint32_t r2_y3 = lo;
         mulhilo(kPhiloxB, r2_y2, hi, lo);  // round 3, the varying product
-        y0[j] = hi ^ c.z0k;
-        y1[j] = lo;
-        y2[j] = r2_y3 ^ c.z2k;
-        y3[j] = c.z3;
+        y0[k] = hi ^ pc.z0k;
+        y1[k] = lo;
+        y2[k] = r2_y3 ^ pc.z2k;
+        y3[k] = pc.z3;
     }
 #pragma unroll
     for (int r = 3; r < 10; ++r) {
         const uint32_t rk0 = k0 + (uint32_t)r * kWeyl0;
         const uint32_t rk1 = k1 + (uint32_t)r * kWeyl1;
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
+        for (int k = 0; k < G; ++k) {
             uint32_t h0, l0, h1, l1;
-            mulhilo(kPhiloxA, y0[j], h0, l0);
-            mulhilo(kPhiloxB, y2[j], h1, l1);
-            const uint32_t n0 = h1 ^ y1[j] ^ rk0;
-            const uint32_t n2 = h0 ^ y3[j] ^ rk1;
-            y0[j] = n0;
-            y1[j] = l1;
-            y2[j] = n2;
-            y3[j] = l0;
+            mulhilo(kPhiloxA, y0[k], h0, l0);
+            mulhilo(kPhiloxB, y2[k], h1, l1);
+            const uint32_t n0 = h1 ^ y1[k] ^ rk0;
+            const uint32_t n2 = h0 ^ y3[k] ^ rk1;
+            y0[k] = n0;
+            y1[k] = l1;
+            y2[k] = n2;
+            y3[k] = l0;
         }
     }
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        out[4 * j + 0] = y0[j];
-        out[4 * j + 1] = y1[j];
-        out[4 * j + 2] = y2[j];
-        out[4 * j + 3] = y3[j];
+    for (int k = 0; k < G; ++k) {
+        o[k][0] = y0[k];
+        o[k][1] = y1[k];
+        o[k][2] = y2[k];
+        o[k][3] = y3[k];
     }
 }
 
@@ -144,12 +149,15 @@ __device__ __forceinline__ void philox4x32_10(uint32_t c0, uint32_t c1, uint32_t
     out[3] = c3;
 }
 
-// The call of site-group q (= colour-plane index >> 2) in the sweep's counter layout
-// (sweep, q low 32, colour, q high 32).
-__device__ __forceinline__ void site_philox(uint64_t q, uint32_t sweep, uint32_t colour, uint64_t key,
-                                            uint32_t out[4])
+// Hot start of plane word g: a site is +1 iff its uniform drawn with sweep slot
+// 0xFFFFFFFF is below 2^31, i.e. iff its bit of R_0 (the top bit plane) is 0; so
+// the word of +1 bits is ~R_0, one call per word.
+__device__ __forceinline__ uint32_t hot_start_word(uint64_t g, uint32_t colour, uint64_t key)
 {
-    philox4x32_10(sweep, (uint32_t)q, colour, (uint32_t)(q >> 32), key, out);
+    const uint64_t q = 8 * g;
+    uint32_t out[4];
+    philox4x32_10(0xFFFFFFFFu, (uint32_t)q, colour, (uint32_t)(q >> 32), key, out);
+    return ~out[0];
 }
 
 }  // namespace ising

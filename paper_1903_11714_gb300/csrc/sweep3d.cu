@@ -4,10 +4,10 @@
 // (Sec. 3) and its conclusion states that the checkerboard algorithm carries
 // over to three dimensions; this file is that generalisation for the cubic
 // L x L x L torus.  Every rule of the 2D sweep is kept (colour order black then
-// white, h = sigma * nn, flip iff h <= 0 or x < T_h, integer thresholds, Philox
-// draws keyed by plane index); the neighbourhood has six sites, so the per-word
-// neighbour count is a 6-input bitwise adder and three thresholds (h = 2, 4, 6)
-// are tested.
+// white, h = sigma * nn, flip iff h <= 0 or U < T_h, integer thresholds, bit-plane
+// Philox uniforms keyed by plane index); the neighbourhood has six sites, so the
+// per-word neighbour count is a 6-input bitwise adder and three thresholds
+// (h = 2, 4, 6) are tested.
 //
 // GB300 mapping: a persistent grid (two 256-thread CTAs per SM) walks groups of
 // four adjacent words (one 16-byte vector load per neighbour row through the
@@ -17,47 +17,71 @@
 #include <cstdint>
 
 #include "ising_internal.cuh"
-#include "philox.cuh"
+#include "word_update.cuh"
 #include "sweep3d.cuh"
 
 namespace ising {
 namespace {
 
-constexpr uint32_t kInitSweep3 = 0xFFFFFFFFu;
 constexpr int kThreads3 = 256;
 
-// New value of one 32-site target word from its six neighbour words.
-__device__ __forceinline__ uint32_t update_word3d(uint32_t t, uint32_t up, uint32_t dn, uint32_t no, uint32_t so,
-                                                  uint32_t same, uint32_t hz, uint32_t q_lo, const PhiloxWordConsts& pc,
-                                                  const CubicDesc& d)
+// New values of G adjacent 32-site target words t[k] (in place) from their six
+// neighbour words; q_lo[k] = 8 * (plane word index) of word k.  With COUNT, adds
+// the fused observables as in 2D (word_update.cuh): ups += set bits of the new
+// target and the `same` source words; anti += anti-aligned bonds after the update,
+// from the adder bits: a site with n anti-aligned neighbours has n if it stays and
+// 6 - n if it flips.  Sites with n >= 3 always flip, so the sum over the flip mask
+// f of (6 - 2n) needs, besides popc(f), only the tested classes n = 1 (b0 alone)
+// and n = 2 (b1 alone) among the flipped sites.
+template <int G, bool COUNT>
+__device__ __forceinline__ void update_words3d(uint32_t t[G], const uint32_t up[G], const uint32_t dn[G],
+                                               const uint32_t no[G], const uint32_t so[G], const uint32_t same[G],
+                                               const uint32_t hz[G], const uint32_t q_lo[G],
+                                               const PhiloxWordConsts& pc, const CubicDesc& d, uint32_t& ups,
+                                               uint32_t& anti)
 {
-    // anti-aligned neighbour bits and their 6-input sum n = 4*b2 + 2*b1 + b0:
-    // two full adders over three inputs each, then the sum bits added (b0, carry
-    // c3) and the three weight-2 carries added (b1, b2)
-    const uint32_t a0 = t ^ up, a1 = t ^ dn, a2 = t ^ no, a3 = t ^ so, a4 = t ^ same, a5 = t ^ hz;
-    const uint32_t s1 = a0 ^ a1 ^ a2, c1 = (a0 & a1) | (a2 & (a0 ^ a1));
-    const uint32_t s2 = a3 ^ a4 ^ a5, c2 = (a3 & a4) | (a5 & (a3 ^ a4));
-    const uint32_t b0 = s1 ^ s2, c3 = s1 & s2;
-    const uint32_t b1 = c1 ^ c2 ^ c3;
-    const uint32_t b2 = (c1 & c2) | (c3 & (c1 ^ c2));
-
-    uint32_t x[32];
-    philox_word8(q_lo, pc, d.key, x);
-    // threshold tests as carry chains (sub.cc sets the carry iff x >= t; addc
-    // shifts it into the mask), one chain per threshold
-    uint32_t g2 = 0, g4 = 0, g6 = 0;
+    const uint32_t thr[3] = {d.t2, d.t4, d.t6};
+    const uint32_t zero2 = (d.t2 == 0u && d.all2 == 0u) ? ~0u : 0u;
+    const uint32_t zero4 = (d.t4 == 0u && d.all4 == 0u) ? ~0u : 0u;
+    const uint32_t zero6 = (d.t6 == 0u && d.all6 == 0u) ? ~0u : 0u;
+    uint32_t always[G], und[G], lt[G], selA[G], selB[G];
 #pragma unroll
-    for (int b = 31; b >= 0; --b) {
-        asm("{\n\t.reg .u32 d;\n\tsub.cc.u32 d, %1, %2;\n\taddc.u32 %0, %0, %0;\n\t}" : "+r"(g2) : "r"(x[b]), "r"(d.t2));
-        asm("{\n\t.reg .u32 d;\n\tsub.cc.u32 d, %1, %2;\n\taddc.u32 %0, %0, %0;\n\t}" : "+r"(g4) : "r"(x[b]), "r"(d.t4));
-        asm("{\n\t.reg .u32 d;\n\tsub.cc.u32 d, %1, %2;\n\taddc.u32 %0, %0, %0;\n\t}" : "+r"(g6) : "r"(x[b]), "r"(d.t6));
+    for (int k = 0; k < G; ++k) {
+        // anti-aligned neighbour bits and their 6-input sum n = 4*b2 + 2*b1 + b0:
+        // two full adders over three inputs each, then the sum bits added (b0,
+        // carry c3) and the three weight-2 carries added (b1, b2)
+        const uint32_t a0 = t[k] ^ up[k], a1 = t[k] ^ dn[k], a2 = t[k] ^ no[k];
+        const uint32_t a3 = t[k] ^ so[k], a4 = t[k] ^ same[k], a5 = t[k] ^ hz[k];
+        const uint32_t s1 = a0 ^ a1 ^ a2, c1 = (a0 & a1) | (a2 & (a0 ^ a1));
+        const uint32_t s2 = a3 ^ a4 ^ a5, c2 = (a3 & a4) | (a5 & (a3 ^ a4));
+        const uint32_t b0 = s1 ^ s2, c3 = s1 & s2;
+        const uint32_t b1 = c1 ^ c2 ^ c3;
+        const uint32_t b2 = (c1 & c2) | (c3 & (c1 ^ c2));
+        // h = 6 - 2n: n >= 3 (h <= 0) always; n = 2 (h = 2): U < T2; n = 1 (h = 4):
+        // U < T4; n = 0 (h = 6): U < T6
+        always[k] = b2 | (b1 & b0);
+        const uint32_t h2 = b1 & ~b0 & ~b2, h4 = b0 & ~b1 & ~b2, h6 = ~(b0 | b1 | b2);
+        lt[k] = (h2 & d.all2) | (h4 & d.all4) | (h6 & d.all6);
+        und[k] = (h2 & ~(d.all2 | zero2)) | (h4 & ~(d.all4 | zero4)) | (h6 & ~(d.all6 | zero6));
+        selA[k] = h2;
+        selB[k] = h4;
+        if (COUNT) {
+            // sum of n, minus the always-flipped sites' 2 (b0) + 4 (b1) + 8 (b2) parts
+            ups += __popc(same[k]);
+            anti += __popc(b0) + 2u * __popc(b1) - 4u * __popc(b2) - 2u * __popc(b0 & (b1 | b2)) -
+                    4u * __popc(b1 & (b0 | b2));
+        }
     }
-    const uint32_t q2 = d.all2 | ~g2, q4 = d.all4 | ~g4, q6 = d.all6 | ~g6;
-    // h = 6 - 2n: n >= 3 (h <= 0) always; n = 2 (h = 2): x < T2; n = 1 (h = 4):
-    // x < T4; n = 0 (h = 6): x < T6.  T6 <= T4 <= T2, so q6 is inside q4 inside q2
-    // and each of q2, q4, q6 may be ORed over a superset of its own class.
-    const uint32_t flip = b2 | (b1 & (b0 | q2)) | (b0 & q4) | q6;
-    return t ^ flip;
+    bitsliced_below<G, 3>(und, lt, selA, selB, q_lo, pc, d.key, thr);
+#pragma unroll
+    for (int k = 0; k < G; ++k) {
+        const uint32_t f = always[k] | lt[k];
+        t[k] ^= f;
+        if (COUNT) {
+            ups += __popc(t[k]);
+            anti += 6u * __popc(f) - 2u * __popc(lt[k] & selB[k]) - 4u * __popc(lt[k] & selA[k]);
+        }
+    }
 }
 
 template <int G>
@@ -221,24 +245,21 @@ __global__ void __launch_bounds__(NT, 2) cubic_half_sweep_kernel(const __grid_co
         const uint64_t q0 = 8ull * (uint64_t)(row + w);
         const PhiloxWordConsts pc =
             q_small ? pc_all : philox_consts(d.key, (uint32_t)(q0 >> 32), sweep, (uint32_t)colour);
-        uint32_t nw[G];
+        uint32_t nw[G], ql[G];
 #pragma unroll
-        for (int k = 0; k < G; ++k)
-            nw[k] = update_word3d(t[k], n.up[k], n.dn[k], n.no[k], n.so[k], n.sm[k], n.hz[k], (uint32_t)q0 + 8u * k,
-                                  pc, d);
+        for (int k = 0; k < G; ++k) {
+            nw[k] = t[k];
+            ql[k] = (uint32_t)q0 + 8u * k;
+        }
+        if (colour == 1)
+            update_words3d<G, true>(nw, n.up, n.dn, n.no, n.so, n.sm, n.hz, ql, pc, d, ups, anti);
+        else
+            update_words3d<G, false>(nw, n.up, n.dn, n.no, n.so, n.sm, n.hz, ql, pc, d, ups, anti);
         if constexpr (G == 4) {
             *reinterpret_cast<uint4*>(trow) = make_uint4(nw[0], nw[1], nw[2], nw[3]);
         } else {
 #pragma unroll
             for (int k = 0; k < G; ++k) trow[k] = nw[k];
-        }
-        if (colour == 1) {
-#pragma unroll
-            for (int k = 0; k < G; ++k) {
-                ups += __popc(nw[k]) + __popc(n.sm[k]);
-                anti += __popc(nw[k] ^ n.up[k]) + __popc(nw[k] ^ n.dn[k]) + __popc(nw[k] ^ n.no[k]) +
-                        __popc(nw[k] ^ n.so[k]) + __popc(nw[k] ^ n.sm[k]) + __popc(nw[k] ^ n.hz[k]);
-            }
         }
         wg += step_w;
         j += step_j;
@@ -292,7 +313,7 @@ __global__ void cubic_set_pair(int64_t* p, int64_t a, int64_t b)
     p[1] = b;
 }
 
-// Start state: hot = bit (x < 2^31) of the draw with sweep slot 0xFFFFFFFF; cold = all +1.
+// Start state: hot = sites whose uniform with sweep slot 0xFFFFFFFF is below 2^31 (~R_0); cold = all +1.
 __global__ void cubic_init_kernel(uint32_t* black, uint32_t* white, int64_t L, uint64_t key, int start)
 {
     const int64_t W = L / 64, words = L * L * W;
@@ -305,16 +326,8 @@ __global__ void cubic_init_kernel(uint32_t* black, uint32_t* white, int64_t L, u
             plane[e] = 0xFFFFFFFFu;
             continue;
         }
-        const int64_t r = e / W, w = e - r * W;
-        const uint64_t q0 = (uint64_t)r * (uint64_t)(L / 8) + 8ull * (uint64_t)w;
-        uint32_t bits = 0;
-        for (int j = 0; j < 8; ++j) {
-            uint32_t x[4];
-            site_philox(q0 + j, kInitSweep3, (uint32_t)c, key, x);
-#pragma unroll
-            for (int m = 0; m < 4; ++m) bits |= (x[m] < 0x80000000u ? 1u : 0u) << (4 * j + m);
-        }
-        plane[e] = bits;
+        // plane word e = r * W + w holds plane indices 32 e .. 32 e + 31
+        plane[e] = hot_start_word((uint64_t)e, (uint32_t)c, key);
     }
 }
 

@@ -4,9 +4,10 @@
 // checkerboard rules (Sec. 3.1, Algorithms 1-2) and six neighbours per site.
 // Layout: two bit planes (colour c = (i+j+k) & 1), each L*L rows of W = L/64
 // words; row r = i*L + j, bit b of word w of row r of plane c is the site
-// (i, j, 2(32w+b) + ((i+j+c) & 1)), 1 = +1.  Plane index p = r*(L/2) + 32w + b;
-// uniform = output word (p & 3) of Philox4x32-10 with counter
-// (sweep, q low, c, q high), q = p >> 2, key = seed.
+// (i, j, 2(32w+b) + ((i+j+c) & 1)), 1 = +1.  Plane index p = r*(L/2) + 32w + b,
+// plane word r*W + w; its uniforms are the 2D ones (philox.cuh): bit b of the 32
+// random words of calls q = 8 (r*W + w) + 0..7, counter (sweep, q low, c, q high),
+// key = seed.
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -25,7 +26,7 @@ struct CubicDesc {
 
 constexpr int64_t kCubicMaxL = 8192;
 
-// Largest cubic side whose plane index q = p >> 2 stays below 2^32 (so the
+// Cubic sides whose Philox call index q = 8 (p >> 5) stays below 2^32 (so the
 // per-launch Philox constants hold for every word).
 __host__ __device__ inline bool cubic_q_small(int64_t L) { return (uint64_t)L * L * L <= (1ull << 35); }
 

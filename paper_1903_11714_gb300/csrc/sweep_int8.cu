@@ -4,16 +4,16 @@
 // bit-packed kernel, so both reach the same chain bit for bit.
 //
 // The start-state kernel works on 8-byte chunks (columns 8g .. 8g+7): the four
-// sites of each colour in a chunk share one Philox call (q = i*L/8 + g).  The
-// half-sweep works on 64-byte row segments (32 target sites, 8 interleaved calls)
-// when L % 64 == 0, else on 8-byte chunks.
+// sites of each colour in a chunk lie in one plane word and take their start spins
+// from its first random word.  The half-sweep works on 64-byte row segments (the
+// 32 target sites of one plane word) when L % 64 == 0, else on 8-byte chunks; both
+// run the bit-sliced test of word_update.cuh on per-site class masks.
 #include "ising_internal.cuh"
-#include "philox.cuh"
+#include "word_update.cuh"
 
 namespace ising {
 namespace {
 
-constexpr uint32_t kInitSweep = 0xFFFFFFFFu;
 
 __device__ __forceinline__ int sbyte(uint64_t v, int k)
 {
@@ -31,13 +31,14 @@ __global__ void int8_init_kernel(int8_t* lat, int64_t L, uint64_t key, int start
         if (start == 1) {
             v = 0x0101010101010101ull;
         } else {
-            const uint64_t q = (uint64_t)i * (uint64_t)(L / 8) + (uint64_t)g;
+            // the chunk's 4 sites of each colour have plane indices p0 .. p0+3, all in
+            // plane word p0 >> 5 (p0 is a multiple of 4)
+            const uint64_t p0 = (uint64_t)i * (uint64_t)(L / 2) + 4ull * (uint64_t)g;
             for (int c = 0; c < 2; ++c) {
-                uint32_t x[4];
-                site_philox(q, kInitSweep, (uint32_t)c, key, x);
+                const uint32_t up_bits = hot_start_word(p0 >> 5, (uint32_t)c, key) >> (p0 & 31);
                 const int r = (int)((i + c) & 1);
                 for (int b = 0; b < 4; ++b) {
-                    const uint64_t byte = x[b] < 0x80000000u ? 0x01ull : 0xFFull;
+                    const uint64_t byte = ((up_bits >> b) & 1u) ? 0x01ull : 0xFFull;
                     v |= byte << (8 * (2 * b + r));
                 }
             }
@@ -80,7 +81,7 @@ __global__ void int8_half_sweep_seg64_kernel(int8_t* lat, int64_t L, uint64_t ke
 {
     // One thread owns a 64-byte segment of a row: columns 64g .. 64g+63, i.e. the
     // 32 target sites j = 64g + 2b + r (b = 0..31) whose plane indices p = i*L/2 +
-    // 32g + b are served by the eight Philox calls q = i*L/8 + 8g + b/4.
+    // 32g + b form plane word i*L/64 + g, drawn from the calls q = i*L/8 + 8g + 0..7.
     const int64_t G = L / 64;
     const int64_t segs = L * G;
     if (colour == 0 && blockIdx.x == 0 && threadIdx.x == 0) {
@@ -88,6 +89,8 @@ __global__ void int8_half_sweep_seg64_kernel(int8_t* lat, int64_t L, uint64_t ke
         hist_slot[1] = 0;
     }
     const PhiloxWordConsts pc = philox_consts(key, 0u, sweep, (uint32_t)colour);
+    const uint32_t thr[2] = {t2, t4};
+    const uint32_t zero2 = (t2 == 0u && all2 == 0u) ? ~0u : 0u, zero4 = (t4 == 0u && all4 == 0u) ? ~0u : 0u;
     long long m_acc = 0, e_acc = 0;
     for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < segs;
          idx += (int64_t)gridDim.x * blockDim.x) {
@@ -111,16 +114,32 @@ __global__ void int8_half_sweep_seg64_kernel(int8_t* lat, int64_t L, uint64_t ke
         const uint64_t q0 = (uint64_t)i * (uint64_t)(L / 8) + 8ull * (uint64_t)g;
         const PhiloxWordConsts pcw =
             L <= 131072 ? pc : philox_consts(key, (uint32_t)(q0 >> 32), sweep, (uint32_t)colour);
-        uint32_t x[32];
-        philox_word8((uint32_t)q0, pcw, key, x);
-        // threshold tests of the 32 draws (carry flag set iff x >= t)
-        uint32_t g2 = 0, g4 = 0;
+        // per-site classes of the 32 target sites (bit b = site j = 64g + 2b + r):
+        // h <= 0 always flips, h = 2 tests U < T2, h = 4 tests U < T4
+        uint32_t alw = 0, h2m = 0, h4m = 0;
 #pragma unroll
-        for (int b = 31; b >= 0; --b) {
-            asm("{\n\t.reg .u32 d;\n\tsub.cc.u32 d, %1, %2;\n\taddc.u32 %0, %0, %0;\n\t}" : "+r"(g2) : "r"(x[b]), "r"(t2));
-            asm("{\n\t.reg .u32 d;\n\tsub.cc.u32 d, %1, %2;\n\taddc.u32 %0, %0, %0;\n\t}" : "+r"(g4) : "r"(x[b]), "r"(t4));
+        for (int rr = 0; rr < 2; ++rr) {
+            if (rr != r) continue;
+#pragma unroll
+            for (int b = 0; b < 32; ++b) {
+                const int k = 2 * b + rr;
+                const int s = sbyte32(cw[k >> 2], k & 3);
+                const int left = k == 0 ? edge : sbyte32(cw[(k - 1) >> 2], (k - 1) & 3);
+                const int right = k == 63 ? edge : sbyte32(cw[(k + 1) >> 2], (k + 1) & 3);
+                const int h = s * (sbyte32(uw[k >> 2], k & 3) + sbyte32(dw[k >> 2], k & 3) + left + right);
+                alw |= (h <= 0 ? 1u : 0u) << b;
+                h2m |= (h == 2 ? 1u : 0u) << b;
+                h4m |= (h == 4 ? 1u : 0u) << b;
+            }
         }
-        const uint32_t q2 = all2 | ~g2, q4 = all4 | ~g4;
+        // the segment's target sites are plane word i * L/64 + g: q_lo = q0
+        uint32_t lt[1] = {(h2m & all2) | (h4m & all4)};
+        uint32_t und[1] = {(h2m & ~(all2 | zero2)) | (h4m & ~(all4 | zero4))};
+        {
+            const uint32_t sel[1] = {h2m}, ql[1] = {(uint32_t)q0};
+            bitsliced_below<1, 2>(und, lt, sel, sel, ql, pcw, key, thr);
+        }
+        const uint32_t accm = alw | lt[0];
         uint32_t nw[16];
 #pragma unroll
         for (int k = 0; k < 16; ++k) nw[k] = cw[k];
@@ -136,8 +155,7 @@ __global__ void int8_half_sweep_seg64_kernel(int8_t* lat, int64_t L, uint64_t ke
                 const int left = k == 0 ? edge : sbyte32(cw[(k - 1) >> 2], (k - 1) & 3);
                 const int right = k == 63 ? edge : sbyte32(cw[(k + 1) >> 2], (k + 1) & 3);
                 const int nn = sbyte32(uw[k >> 2], k & 3) + sbyte32(dw[k >> 2], k & 3) + left + right;
-                const int h = s * nn;
-                const bool acc = h <= 0 || (h == 2 ? ((q2 >> b) & 1u) : ((q4 >> b) & 1u));
+                const bool acc = (accm >> b) & 1u;
                 if (acc) nw[k >> 2] ^= 0xFEu << (8 * (k & 3));  // 0x01 <-> 0xFF
                 e_here -= (long long)(acc ? -s : s) * nn;
             }
@@ -161,7 +179,7 @@ __global__ void int8_half_sweep_seg64_kernel(int8_t* lat, int64_t L, uint64_t ke
     if (colour == 1) block_add_pair(m_acc, e_acc, hist_slot);
 }
 
-// L % 64 != 0: one thread per 8-byte chunk (4 target sites, one Philox call).
+// L % 64 != 0: one thread per 8-byte chunk (4 target sites, part of one plane word).
 __global__ void int8_half_sweep_chunk8_kernel(int8_t* lat, int64_t L, uint64_t key, uint32_t t2, uint32_t t4, uint32_t all2,
                                        uint32_t all4, uint32_t sweep, int colour, int64_t* hist_slot)
 {
@@ -171,6 +189,9 @@ __global__ void int8_half_sweep_chunk8_kernel(int8_t* lat, int64_t L, uint64_t k
         hist_slot[0] = 0;  // opened here, filled by the colour-1 pass of the same sweep
         hist_slot[1] = 0;
     }
+    const PhiloxWordConsts pc = philox_consts(key, 0u, sweep, (uint32_t)colour);
+    const uint32_t thr[2] = {t2, t4};
+    const uint32_t zero2 = (t2 == 0u && all2 == 0u) ? ~0u : 0u, zero4 = (t4 == 0u && all4 == 0u) ? ~0u : 0u;
     long long m_acc = 0, e_acc = 0;
     for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < chunks;
          idx += (int64_t)gridDim.x * blockDim.x) {
@@ -185,9 +206,31 @@ __global__ void int8_half_sweep_chunk8_kernel(int8_t* lat, int64_t L, uint64_t k
         const int64_t edge_col = r ? (g + 1 == G ? 0 : 8 * g + 8) : (g == 0 ? L - 1 : 8 * g - 1);
         const int edge = row[edge_col];
 
-        const uint64_t q = (uint64_t)i * (uint64_t)(L / 8) + (uint64_t)g;
-        uint32_t x[4];
-        site_philox(q, sweep, (uint32_t)colour, key, x);
+        // the chunk's 4 target sites have plane indices p0 .. p0+3 (p0 % 4 == 0), the
+        // bits pos .. pos+3 of plane word p0 >> 5
+        const uint64_t p0 = (uint64_t)i * (uint64_t)(L / 2) + 4ull * (uint64_t)g;
+        const int pos = (int)(p0 & 31);
+        const uint64_t qw = 8 * (p0 >> 5);
+        const PhiloxWordConsts pcw =
+            (qw >> 32) == 0 ? pc : philox_consts(key, (uint32_t)(qw >> 32), sweep, (uint32_t)colour);
+        uint32_t alw = 0, h2m = 0, h4m = 0;
+        for (int b = 0; b < 4; ++b) {
+            const int k = 2 * b + r;
+            const int s = sbyte(cur, k);
+            const int left = k == 0 ? edge : sbyte(cur, k - 1);
+            const int right = k == 7 ? edge : sbyte(cur, k + 1);
+            const int h = s * (sbyte(upv, k) + sbyte(dnv, k) + left + right);
+            alw |= (h <= 0 ? 1u : 0u) << (pos + b);
+            h2m |= (h == 2 ? 1u : 0u) << (pos + b);
+            h4m |= (h == 4 ? 1u : 0u) << (pos + b);
+        }
+        uint32_t lt[1] = {(h2m & all2) | (h4m & all4)};
+        uint32_t und[1] = {(h2m & ~(all2 | zero2)) | (h4m & ~(all4 | zero4))};
+        {
+            const uint32_t sel[1] = {h2m}, ql[1] = {(uint32_t)qw};
+            bitsliced_below<1, 2>(und, lt, sel, sel, ql, pcw, key, thr);
+        }
+        const uint32_t accm = alw | lt[0];
 
         uint64_t nv = cur;
         long long e_here = 0;
@@ -197,14 +240,7 @@ __global__ void int8_half_sweep_chunk8_kernel(int8_t* lat, int64_t L, uint64_t k
             const int left = k == 0 ? edge : sbyte(cur, k - 1);
             const int right = k == 7 ? edge : sbyte(cur, k + 1);
             const int nn = sbyte(upv, k) + sbyte(dnv, k) + left + right;
-            const int h = s * nn;
-            bool acc;
-            if (h <= 0)
-                acc = true;
-            else if (h == 2)
-                acc = all2 || x[b] < t2;
-            else
-                acc = all4 || x[b] < t4;
+            const bool acc = (accm >> (pos + b)) & 1u;
             const int snew = acc ? -s : s;
             if (acc) nv ^= (0xFEull << (8 * k));  // 0x01 <-> 0xFF
             e_here -= (long long)snew * nn;

@@ -13,8 +13,9 @@
 //
 // Per 32-site word: n_anti (number of anti-aligned neighbours, 0..4) comes from a
 // bitwise 4-input adder; h = sigma * nn = 4 - 2 n_anti.  h <= 0 flips always;
-// h = 2 flips iff the site's Philox word is below T2, h = 4 iff below T4
-// (Sec. 3.1 acceptance min{1, exp(-2 beta h)} as an integer threshold).
+// h = 2 flips iff the site's uniform U is below T2, h = 4 iff below T4 (Sec. 3.1
+// acceptance min{1, exp(-2 beta h)} as an integer threshold), with U compared bit
+// plane by bit plane on whole words (word_update.cuh).
 //
 // Each persistent CTA walks the tile table: a tile is `tile_rows` full rows of
 // one lattice.  Thread 0 stages the tile's source rows (plus the halo rows above
@@ -62,6 +63,16 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
         : "r"(smem_addr(bar)), "r"(parity)
         : "memory");
     return done != 0;
+}
+
+// A 16-byte shared-memory load the compiler may not merge with an earlier one (so a
+// value read before a long computation is read again instead of held in registers).
+__device__ __forceinline__ uint4 ld_shared_v4(const uint32_t* p)
+{
+    uint4 v;
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+    asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(a));
+    return v;
 }
 
 // Bounded wait: returns false after `limit` SM clocks without completion.
@@ -171,8 +182,14 @@ __device__ __forceinline__ void issue_tile(const LatticeDesc& d, int local_tile,
     bulk_copy_g2s(s_tgt, tgt + (size_t)i0 * W, row_bytes * TR, bar);
 }
 
+// Register budgets: the single-lattice instance reads its descriptor from a
+// __grid_constant__ parameter, so the key, thresholds and Philox constants sit in
+// uniform registers and 2 CTAs of 256 fit at <= 128 registers; the general instance
+// loads them per tile into ordinary registers and is allowed more (one CTA per
+// 256 threads per SM), which is faster than spilling inside the random-number loop.
 template <int NT, bool ONE>
-__global__ void __launch_bounds__(NT, (ISING_SWEEP_THREADS_PER_SM / NT > 0 ? ISING_SWEEP_THREADS_PER_SM / NT : 1))
+__global__ void __launch_bounds__(NT, (ONE ? (ISING_SWEEP_THREADS_PER_SM / NT > 0 ? ISING_SWEEP_THREADS_PER_SM / NT : 1)
+                                           : (256 / NT > 0 ? 256 / NT : 1)))
     packed_half_sweep_kernel(TileTable tt, const __grid_constant__ LatticeDesc one, int colour, int step,
                              int* status, int stage_words_max, long long wait_limit, uint32_t extra_tx)
 {
@@ -315,20 +332,31 @@ __global__ void __launch_bounds__(NT, (ISING_SWEEP_THREADS_PER_SM / NT > 0 ? ISI
                         q_small ? pc_tile : philox_consts(key, (uint32_t)(q0 >> 32), sweep, (uint32_t)colour);
                     const uint32_t up[4] = {upq.x, upq.y, upq.z, upq.w}, dn[4] = {dnq.x, dnq.y, dnq.z, dnq.w};
                     const uint32_t sm[4] = {smq.x, smq.y, smq.z, smq.w}, tg[4] = {tgq.x, tgq.y, tgq.z, tgq.w};
-                    uint32_t nw[4];
+                    const uint32_t ql[4] = {(uint32_t)q0, (uint32_t)q0 + 8u, (uint32_t)q0 + 16u, (uint32_t)q0 + 24u};
+                    // the random-number loop runs on two words at a time: a thread stops
+                    // drawing once both are decided, and a warp once all its lanes are, so
+                    // the smaller group draws fewer calls at warp level than all four
+                    // words together would (the pair interleaves two calls)
+                    uint32_t f[4];
 #pragma unroll
-                    for (int k = 0; k < 4; ++k)
-                        nw[k] = update_word(tg[k], up[k], dn[k], sm[k], hz[k], (uint32_t)q0 + 8u * k, pc, key, t2, t4,
-                                            all2, all4);
-                    *reinterpret_cast<uint4*>(out_plane + (size_t)i * W + w) = make_uint4(nw[0], nw[1], nw[2], nw[3]);
-                    if (colour == 1) {
-#pragma unroll
-                        for (int k = 0; k < 4; ++k) {
-                            ups += __popc(nw[k]) + __popc(sm[k]);
-                            anti += __popc(nw[k] ^ up[k]) + __popc(nw[k] ^ dn[k]) + __popc(nw[k] ^ sm[k]) +
-                                    __popc(nw[k] ^ hz[k]);
-                        }
+                    for (int hh = 0; hh < 2; ++hh) {
+                        const uint32_t a_t[2] = {tg[2 * hh], tg[2 * hh + 1]}, a_u[2] = {up[2 * hh], up[2 * hh + 1]};
+                        const uint32_t a_d[2] = {dn[2 * hh], dn[2 * hh + 1]}, a_s[2] = {sm[2 * hh], sm[2 * hh + 1]};
+                        const uint32_t a_h[2] = {hz[2 * hh], hz[2 * hh + 1]}, a_q[2] = {ql[2 * hh], ql[2 * hh + 1]};
+                        uint32_t a_f[2];
+                        if (colour == 1)
+                            flip_masks<2, true>(a_t, a_u, a_d, a_s, a_h, a_q, pc, key, t2, t4, all2, all4, a_f, ups, anti);
+                        else
+                            flip_masks<2, false>(a_t, a_u, a_d, a_s, a_h, a_q, pc, key, t2, t4, all2, all4, a_f, ups, anti);
+                        f[2 * hh] = a_f[0];
+                        f[2 * hh + 1] = a_f[1];
                     }
+                    // the target words again from shared memory, so that they need not
+                    // stay in registers across the random-number loop
+                    const uint4 tq = ld_shared_v4(s_tgt + (size_t)r * W + w);
+                    const uint4 nq = make_uint4(tq.x ^ f[0], tq.y ^ f[1], tq.z ^ f[2], tq.w ^ f[3]);
+                    *reinterpret_cast<uint4*>(out_plane + (size_t)i * W + w) = nq;
+                    if (colour == 1) ups += __popc(nq.x) + __popc(nq.y) + __popc(nq.z) + __popc(nq.w);
                     r += step_r;
                     w4 += step_w;
                     if (w4 >= W4) {
@@ -363,15 +391,19 @@ __global__ void __launch_bounds__(NT, (ISING_SWEEP_THREADS_PER_SM / NT > 0 ? ISI
                     const uint64_t q0 = (uint64_t)i * (uint64_t)(L >> 3) + 8ull * (uint64_t)w;
                     const PhiloxWordConsts pc =
                         q_small ? pc_tile : philox_consts(key, (uint32_t)(q0 >> 32), sweep, (uint32_t)colour);
-                    uint2 nw;
-                    nw.x = update_word(tgp.x, upp.x, dnp.x, smp.x, hz0, (uint32_t)q0, pc, key, t2, t4, all2, all4);
-                    nw.y = update_word(tgp.y, upp.y, dnp.y, smp.y, hz1, (uint32_t)q0 + 8u, pc, key, t2, t4, all2, all4);
-                    *reinterpret_cast<uint2*>(out_plane + (size_t)i * W + w) = nw;
-                    if (colour == 1) {
-                        ups += __popc(nw.x) + __popc(smp.x) + __popc(nw.y) + __popc(smp.y);
-                        anti += __popc(nw.x ^ upp.x) + __popc(nw.x ^ dnp.x) + __popc(nw.x ^ smp.x) + __popc(nw.x ^ hz0)
-                              + __popc(nw.y ^ upp.y) + __popc(nw.y ^ dnp.y) + __popc(nw.y ^ smp.y) + __popc(nw.y ^ hz1);
+                    uint32_t f[2];
+                    {
+                        const uint32_t t2w[2] = {tgp.x, tgp.y};
+                        const uint32_t u2[2] = {upp.x, upp.y}, d2[2] = {dnp.x, dnp.y}, m2[2] = {smp.x, smp.y};
+                        const uint32_t z2[2] = {hz0, hz1}, ql[2] = {(uint32_t)q0, (uint32_t)q0 + 8u};
+                        if (colour == 1)
+                            flip_masks<2, true>(t2w, u2, d2, m2, z2, ql, pc, key, t2, t4, all2, all4, f, ups, anti);
+                        else
+                            flip_masks<2, false>(t2w, u2, d2, m2, z2, ql, pc, key, t2, t4, all2, all4, f, ups, anti);
                     }
+                    const uint2 nw = make_uint2(tgp.x ^ f[0], tgp.y ^ f[1]);
+                    *reinterpret_cast<uint2*>(out_plane + (size_t)i * W + w) = nw;
+                    if (colour == 1) ups += __popc(nw.x) + __popc(nw.y);
                     r += step_r;
                     w2 += step_w;
                     if (w2 >= W2) {
@@ -402,12 +434,17 @@ __global__ void __launch_bounds__(NT, (ISING_SWEEP_THREADS_PER_SM / NT > 0 ? ISI
                 const uint64_t q0 = (uint64_t)i * (uint64_t)(L >> 3) + 8ull * (uint64_t)w;
                 const PhiloxWordConsts pc =
                     q_small ? pc_tile : philox_consts(key, (uint32_t)(q0 >> 32), sweep, (uint32_t)colour);
-                const uint32_t nw = update_word(tw, up, down, same, hz, (uint32_t)q0, pc, key, t2, t4, all2, all4);
-                out_plane[(size_t)i * W + w] = nw;
-                if (colour == 1) {
-                    ups += __popc(nw) + __popc(same);
-                    anti += __popc(nw ^ up) + __popc(nw ^ down) + __popc(nw ^ same) + __popc(nw ^ hz);
+                uint32_t f[1];
+                {
+                    const uint32_t t1[1] = {tw};
+                    const uint32_t u1[1] = {up}, d1[1] = {down}, m1[1] = {same}, z1[1] = {hz}, ql[1] = {(uint32_t)q0};
+                    if (colour == 1)
+                        flip_masks<1, true>(t1, u1, d1, m1, z1, ql, pc, key, t2, t4, all2, all4, f, ups, anti);
+                    else
+                        flip_masks<1, false>(t1, u1, d1, m1, z1, ql, pc, key, t2, t4, all2, all4, f, ups, anti);
                 }
+                out_plane[(size_t)i * W + w] = tw ^ f[0];
+                if (colour == 1) ups += __popc(tw ^ f[0]);
                 r += step_r;
                 w += step_w;
                 if (w >= W) {
@@ -501,18 +538,23 @@ cudaError_t packed_set_smem_limit(int threads, size_t bytes)
     }
 }
 
-cudaError_t packed_occupancy(int threads, size_t smem, int* blocks_per_sm)
+template <int NT>
+cudaError_t occupancy_nt(size_t smem, int* blocks_per_sm, bool one)
+{
+    return one ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, packed_half_sweep_kernel<NT, true>, NT, smem)
+               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, packed_half_sweep_kernel<NT, false>, NT,
+                                                               smem);
+}
+
+cudaError_t packed_occupancy(int threads, size_t smem, int* blocks_per_sm, bool one)
 {
     switch (threads) {
     case 128:
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, packed_half_sweep_kernel<128, false>, 128,
-                                                             smem);
+        return occupancy_nt<128>(smem, blocks_per_sm, one);
     case 256:
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, packed_half_sweep_kernel<256, false>, 256,
-                                                             smem);
+        return occupancy_nt<256>(smem, blocks_per_sm, one);
     case 512:
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, packed_half_sweep_kernel<512, false>, 512,
-                                                             smem);
+        return occupancy_nt<512>(smem, blocks_per_sm, one);
     default:
         return cudaErrorInvalidValue;
     }

@@ -47,13 +47,18 @@ __global__ void __launch_bounds__(NT, 1) packed_resident_kernel(const __grid_con
                 const uint64_t q0 = (uint64_t)i * (uint64_t)(L >> 3) + 8ull * (uint64_t)w;
                 const PhiloxWordConsts pc =
                     q_small ? pc_all : philox_consts(key, (uint32_t)(q0 >> 32), sweep, (uint32_t)colour);
-                const uint32_t nw =
-                    update_word(tgt[idx], up, down, same, hz, (uint32_t)q0, pc, key, d.t2, d.t4, d.all2, d.all4);
-                tgt[idx] = nw;
-                if (colour == 1) {
-                    ups += __popc(nw) + __popc(same);
-                    anti += __popc(nw ^ up) + __popc(nw ^ down) + __popc(nw ^ same) + __popc(nw ^ hz);
+                const uint32_t tw = tgt[idx];
+                uint32_t f[1];
+                {
+                    const uint32_t t1[1] = {tw};
+                    const uint32_t u1[1] = {up}, d1[1] = {down}, m1[1] = {same}, z1[1] = {hz}, ql[1] = {(uint32_t)q0};
+                    if (colour == 1)
+                        flip_masks<1, true>(t1, u1, d1, m1, z1, ql, pc, key, d.t2, d.t4, d.all2, d.all4, f, ups, anti);
+                    else
+                        flip_masks<1, false>(t1, u1, d1, m1, z1, ql, pc, key, d.t2, d.t4, d.all2, d.all4, f, ups, anti);
                 }
+                tgt[idx] = tw ^ f[0];
+                if (colour == 1) ups += __popc(tw ^ f[0]);
             }
             if (colour == 1) {
                 const uint32_t u = __reduce_add_sync(0xffffffffu, ups);

@@ -1,6 +1,7 @@
-// The update of one 32-site word of the target colour plane (paper Sec. 3.1
+// The Metropolis update of 32-site words of a target colour plane (paper Sec. 3.1
 // acceptance rule on the bit-packed colour planes of Sec. 3.2), shared by the
-// tiled sweep kernel and the single-CTA resident kernel.
+// tiled sweep kernel, the single-CTA resident kernel, the int8 kernel and the
+// three-dimensional sweep.
 #pragma once
 #include <cstdint>
 
@@ -8,38 +9,108 @@
 
 namespace ising {
 
-// New value of one 32-site target word.
-__device__ __forceinline__ uint32_t update_word(uint32_t t, uint32_t up, uint32_t down, uint32_t same,
-                                                uint32_t hz, uint32_t q_lo, const PhiloxWordConsts& pc,
-                                                uint64_t key, uint32_t t2, uint32_t t4, uint32_t all2,
-                                                uint32_t all4)
+// Bit-sliced test U < T_h for the sites of G plane words.  A site's uniform U has
+// bit 31 - k in bit plane R_k of its word (see philox.cuh), so comparing U with
+// its threshold from the top bit down decides the site at the first plane where
+// the two bits differ: U < T there iff the threshold's bit is 1.  Per plane and
+// word that is four logic operations for all 32 sites; planes are drawn four at a
+// time (one Philox call) and drawing stops once no site of the thread's words is
+// undecided -- on average after about three of the eight calls, against eight
+// calls for whole 32-bit uniforms.  The decisions are those of the full 32-bit
+// comparison, bit for bit.
+//
+// und[k]: sites of word k still to test (updated); lt[k]: sites found below their
+// threshold (ORed into).  NTH thresholds t[0..NTH-1] (values min(T, 2^32 - 1)); a
+// site's threshold is t[0] where selA, else t[1] where selB (NTH = 3), else the
+// last one.  Sites whose threshold is 0 or 2^32 must not be in und.
+template <int G, int NTH>
+__device__ __forceinline__ void bitsliced_below(uint32_t und[G], uint32_t lt[G], const uint32_t selA[G],
+                                                const uint32_t selB[G], const uint32_t q_lo[G],
+                                                const PhiloxWordConsts& pc, uint64_t key, const uint32_t (&t)[NTH])
 {
-    // anti-aligned neighbour bits and their 4-input sum n_anti = 4*b2 + 2*b1 + b0
-    const uint32_t au = t ^ up, ad = t ^ down, as = t ^ same, ah = t ^ hz;
-    const uint32_t s0 = au ^ ad, c0 = au & ad;
-    const uint32_t s1 = as ^ ah, c1 = as & ah;
-    const uint32_t b0 = s0 ^ s1, cc = s0 & s1;
-    const uint32_t b1 = c0 ^ c1 ^ cc;
-    const uint32_t b2 = c0 & c1;
-
-    uint32_t x[32];
-    philox_word8(q_lo, pc, key, x);
-    // Threshold tests as carry chains: sub.cc sets the carry flag iff x >= t (no
-    // borrow), and addc doubles the mask and adds that flag, so after 32 steps bit b
-    // of g holds [x[b] >= t]; two instructions per compare, no predicate-to-bit
-    // packing.  q = ~g is the mask of x < t.
-    uint32_t g2 = 0, g4 = 0;
+    uint32_t base[G];
 #pragma unroll
-    for (int b = 31; b >= 0; --b) {
-        asm("{\n\t.reg .u32 d;\n\tsub.cc.u32 d, %1, %2;\n\taddc.u32 %0, %0, %0;\n\t}" : "+r"(g2) : "r"(x[b]), "r"(t2));
-        asm("{\n\t.reg .u32 d;\n\tsub.cc.u32 d, %1, %2;\n\taddc.u32 %0, %0, %0;\n\t}" : "+r"(g4) : "r"(x[b]), "r"(t4));
+    for (int k = 0; k < G; ++k) base[k] = q_lo[k] ^ pc.x0k;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        uint32_t any = 0;
+#pragma unroll
+        for (int k = 0; k < G; ++k) any |= und[k];
+        if (any == 0) break;
+        uint32_t o[G][4];
+        philox_calls<G>(base, (uint32_t)c, pc, key, o);
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            const int bit = 31 - (4 * c + m);
+            // the threshold's bit in this plane, as a mask per threshold
+            uint32_t K[NTH];
+#pragma unroll
+            for (int h = 0; h < NTH; ++h) K[h] = 0u - ((t[h] >> bit) & 1u);
+#pragma unroll
+            for (int k = 0; k < G; ++k) {
+                uint32_t tm;
+                if constexpr (NTH == 2) {
+                    tm = (selA[k] & K[0]) | (~selA[k] & K[1]);
+                } else {
+                    const uint32_t rest = (selB[k] & K[1]) | (~selB[k] & K[2]);
+                    tm = (selA[k] & K[0]) | (~selA[k] & rest);
+                }
+                const uint32_t x = und[k] & (o[k][m] ^ tm);  // decided in this plane
+                lt[k] |= x & tm;                              // ... below: U's bit 0, T's bit 1
+                und[k] &= ~x;
+            }
+        }
     }
-    const uint32_t q2 = all2 | ~g2;
-    const uint32_t q4 = all4 | ~g4;
-    // n_anti >= 2 (h <= 0): always; n_anti == 1 (h = 2): x < T2; n_anti == 0 (h = 4):
-    // x < T4.  T4 <= T2, so q4 is a subset of q2 and ORing q4 everywhere is exact.
-    const uint32_t flip = b1 | b2 | (b0 & q2) | q4;
-    return t ^ flip;
+}
+
+// Flip masks f[k] of G adjacent 32-site target words t[k] from their four
+// neighbour words; q_lo[k] = 8 * (plane word index) of word k.  The caller applies
+// them (t ^ f) -- from a fresh read of the target words if it wants them out of
+// registers during the random-number loop.  With COUNT, adds the fused observables
+// of the updated words except the set bits of the new target words, which the
+// caller adds: ups += set bits of the `same` source words, anti += anti-aligned
+// target-source bonds after the update.  The bond count comes from the adder bits,
+// so the neighbour words need not stay live across the loop: a site with n
+// anti-aligned neighbours keeps n if it stays and has 4 - n if it flips, and f
+// contains every site with n >= 2 (b1 | b2), so the word's total is
+// popc(b0) + 2 popc(b1) + 4 popc(b2) + sum over f of (4 - 2n)
+//   = popc(b0) - 2 popc(b1) - 4 popc(b2) + 4 popc(f) - 2 popc(f & b0).
+// (Unsigned wrap-around is harmless: each thread's total is non-negative.)
+template <int G, bool COUNT>
+__device__ __forceinline__ void flip_masks(const uint32_t t[G], const uint32_t up[G], const uint32_t down[G],
+                                           const uint32_t same[G], const uint32_t hz[G], const uint32_t q_lo[G],
+                                           const PhiloxWordConsts& pc, uint64_t key, uint32_t t2, uint32_t t4,
+                                           uint32_t all2, uint32_t all4, uint32_t f[G], uint32_t& ups, uint32_t& anti)
+{
+    // thresholds 0 (never accept) are taken out of the test like 2^32 (always)
+    const uint32_t zero2 = (t2 == 0u && all2 == 0u) ? ~0u : 0u, zero4 = (t4 == 0u && all4 == 0u) ? ~0u : 0u;
+    const uint32_t thr[2] = {t2, t4};
+    uint32_t und[G], sel[G];
+#pragma unroll
+    for (int k = 0; k < G; ++k) {
+        // anti-aligned neighbour bits and their 4-input sum n = 4*b2 + 2*b1 + b0
+        const uint32_t au = t[k] ^ up[k], ad = t[k] ^ down[k], as = t[k] ^ same[k], ah = t[k] ^ hz[k];
+        const uint32_t s0 = au ^ ad, c0 = au & ad;
+        const uint32_t s1 = as ^ ah, c1 = as & ah;
+        const uint32_t b0 = s0 ^ s1, cc = s0 & s1;
+        const uint32_t b1 = c0 ^ c1 ^ cc;
+        const uint32_t b2 = c0 & c1;
+        // n >= 2 (h <= 0): always; n == 1 (h = 2): U < T2; n == 0 (h = 4): U < T4
+        const uint32_t always = b1 | b2;
+        const uint32_t h2 = b0 & ~always, h4 = ~b0 & ~always;
+        f[k] = always | (h2 & all2) | (h4 & all4);
+        und[k] = (h2 & ~(all2 | zero2)) | (h4 & ~(all4 | zero4));
+        sel[k] = b0;
+        if (COUNT) {
+            ups += __popc(same[k]);
+            anti += __popc(b0) - 2u * __popc(b1) - 4u * __popc(b2);
+        }
+    }
+    bitsliced_below<G, 2>(und, f, sel, sel, q_lo, pc, key, thr);
+    if (COUNT) {
+#pragma unroll
+        for (int k = 0; k < G; ++k) anti += 4u * __popc(f[k]) - 2u * __popc(f[k] & sel[k]);
+    }
 }
 
 }  // namespace ising

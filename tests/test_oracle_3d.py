@@ -47,23 +47,30 @@ def test_accept3d_rule():
 
 
 # ------------------------------------------------------------- RNG keying
-def test_site_word3d_keying():
-    """Site (i,j,k) uses word p & 3 of counter (sweep, q lo, c, q hi), q = p >> 2,
-    p = (i*Y + j)*(Z/2) + (k >> 1)."""
-    seed = 0x1234_5678_9ABC_DEF0
+def _uniform3_from_philox(p, seed, sweep, c):
     key = (seed & 0xFFFFFFFF, seed >> 32)
-    cases = [((4, 6, 8), (0, 0, 0)), ((4, 6, 8), (3, 5, 7)), ((8, 8, 8), (1, 2, 5)),
+    g, b = p >> 5, p & 31
+    u = 0
+    for k in range(32):
+        q = 8 * g + k // 4
+        u |= ((oracle.philox4x32_10((sweep, q & 0xFFFFFFFF, c, q >> 32), key)[k & 3] >> b) & 1) << (31 - k)
+    return u
+
+
+def test_site_word3d_keying():
+    """Site (i,j,k) draws the uniform of plane index p = (i*Y + j)*(Z/2) + (k >> 1):
+    bit p & 31 of the random words R_0 .. R_31 of plane word p >> 5, R_0 the top bit."""
+    seed = 0x1234_5678_9ABC_DEF0
+    cases = [((4, 6, 8), (0, 0, 0)), ((4, 6, 8), (3, 5, 7)), ((8, 8, 8), (1, 2, 5)), ((2, 2, 4), (1, 1, 3)),
              # q passes 2^32: X = Y = 65536, Z = 64
              ((65536, 65536, 64), (65535, 40000, 63)), ((65536, 65536, 64), (33000, 1, 2))]
     for dims, (i, j, k) in cases:
         X, Y, Z = dims
         c = (i + j + k) & 1
         p = (i * Y + j) * (Z // 2) + (k >> 1)
-        q = p >> 2
         for sweep in (0, 9, 0xFFFFFFFF):
-            want = oracle.philox4x32_10((sweep, q & 0xFFFFFFFF, c, q >> 32), key)[p & 3]
-            assert oracle.site_word3d(dims, i, j, k, seed, sweep, c) == want
-    assert ((65535 * 65536 + 40000) * 32) >> 2 >= 1 << 32
+            assert oracle.site_word3d(dims, i, j, k, seed, sweep, c) == _uniform3_from_philox(p, seed, sweep, c)
+    assert 8 * (((65535 * 65536 + 40000) * 32) >> 5) >= 1 << 32  # q = 8 (p >> 5) has a high word
 
 
 def test_3d_row_keying_matches_2d_rows():
@@ -74,9 +81,7 @@ def test_3d_row_keying_matches_2d_rows():
         for c in (0, 1):
             for sweep in (0, 5):
                 p2 = r * (Z // 2) + (k >> 1)
-                q = p2 >> 2
-                want = oracle.philox4x32_10((sweep, q, c, 0), (seed, 0))[p2 & 3]
-                assert oracle.site_word3d((X, Y, Z), i, j, k, seed, sweep, c) == want
+                assert oracle.site_word3d((X, Y, Z), i, j, k, seed, sweep, c) == _uniform3_from_philox(p2, seed, sweep, c)
 
 
 # --------------------------------------------------- exact enumeration pins

@@ -77,18 +77,57 @@ def test_philox_output_statistics():
     assert 150 < chi2 < 380  # 255 dof, far tails only
 
 
-def test_site_word_keying():
-    """Site (i,j) of colour c uses word p & 3 of counter (sweep, q lo, c, q hi), q = p >> 2."""
-    seed = 0xABCDEF0123
+def _uniform_from_philox(p, seed, sweep, c):
+    """U of plane index p restated from the definition: bit b = p & 31 of the 32
+    random words of plane word g = p >> 5, R_k = output k & 3 of the call with
+    counter (sweep, q lo, c, q hi), q = 8g + k // 4; R_0 gives the top bit."""
     key = (seed & 0xFFFFFFFF, seed >> 32)
+    g, b = p >> 5, p & 31
+    u = 0
+    for k in range(32):
+        q = 8 * g + k // 4
+        r = oracle.philox4x32_10((sweep, q & 0xFFFFFFFF, c, q >> 32), key)[k & 3]
+        u |= ((r >> b) & 1) << (31 - k)
+    return u
+
+
+def test_site_word_keying():
+    """Site (i,j) of colour c, plane index p = i*(L/2) + (j>>1), draws the uniform above."""
+    seed = 0xABCDEF0123
     cases = [(64, i, j) for (i, j) in [(0, 0), (0, 1), (1, 0), (5, 37), (63, 63), (31, 6)]]
     # L = 2^18: q passes 2^32 in the lower rows, so q's high word is non-zero
     cases += [(1 << 18, 200000, 12345), (1 << 18, (1 << 18) - 1, (1 << 18) - 2)]
+    # L = 72 (not a multiple of 64): plane words straddle rows
+    cases += [(72, 0, 70), (72, 1, 0), (72, 1, 1), (72, 13, 44)]
     for (L, i, j) in cases:
         c = (i + j) & 1
         p = i * (L // 2) + (j >> 1)
-        q = p >> 2
         for sweep in (0, 7, 0xFFFFFFFF):
-            want = oracle.philox4x32_10((sweep, q & 0xFFFFFFFF, c, q >> 32), key)[p & 3]
-            assert oracle.site_word(L, i, j, seed, sweep, c) == want
-    assert (200000 * (1 << 17)) >> 2 >= 1 << 32
+            assert oracle.site_word(L, i, j, seed, sweep, c) == _uniform_from_philox(p, seed, sweep, c)
+    assert (200000 * (1 << 17)) >> 5 >= 1 << 29
+
+
+def test_site_uniforms_are_uniform():
+    """The transposed uniforms of many sites: each of their 32 bits is a fair coin
+    and the top byte is flat (chi-square, 255 degrees of freedom)."""
+    L = 64
+    u = np.array([oracle.site_word(L, i, j, 99, 3, (i + j) & 1) for i in range(L) for j in range(L)], dtype=np.uint64)
+    n = u.size
+    for bit in range(32):
+        ones = int(((u >> np.uint64(bit)) & np.uint64(1)).sum())
+        assert abs(ones - n / 2) < 5 * np.sqrt(n / 4), bit
+    counts = np.bincount((u >> np.uint64(24)).astype(np.int64), minlength=256)
+    chi2 = ((counts - n / 256) ** 2 / (n / 256)).sum()
+    assert 150 < chi2 < 380
+
+
+def test_hot_start_is_the_top_bit_of_the_first_random_word():
+    """U < 2^31 holds exactly when bit b of R_0 is 0: the hot start needs R_0 only."""
+    L, seed = 64, 12
+    s = oracle.init(L, seed, oracle.HOT)
+    key = (seed, 0)
+    for (i, j) in [(0, 0), (3, 9), (40, 41), (63, 0)]:
+        c = (i + j) & 1
+        p = i * (L // 2) + (j >> 1)
+        r0 = oracle.philox4x32_10((0xFFFFFFFF, 8 * (p >> 5), c, 0), key)[0]
+        assert s[i, j] == (1 if ((r0 >> (p & 31)) & 1) == 0 else -1)
