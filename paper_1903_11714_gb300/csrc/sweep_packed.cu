@@ -15,7 +15,9 @@
 // bitwise 4-input adder; h = sigma * nn = 4 - 2 n_anti.  h <= 0 flips always;
 // h = 2 flips iff the site's uniform U is below T2, h = 4 iff below T4 (Sec. 3.1
 // acceptance min{1, exp(-2 beta h)} as an integer threshold), with U compared bit
-// plane by bit plane on whole words (word_update.cuh).
+// plane by bit plane on whole words (word_update.cuh).  Each word draws two Philox
+// calls in step with its warp; the ~10 % of words with sites still undecided
+// after them finish from a per-warp queue (update_tile).
 //
 // Each persistent CTA walks the tile table: a tile is `tile_rows` full rows of
 // one lattice.  Thread 0 stages the tile's source rows (plus the halo rows above
@@ -182,6 +184,181 @@ __device__ __forceinline__ void issue_tile(const LatticeDesc& d, int local_tile,
     bulk_copy_g2s(s_tgt, tgt + (size_t)i0 * W, row_bytes * TR, bar);
 }
 
+template <int G>
+__device__ __forceinline__ void load_group(const uint32_t* p, uint32_t v[G])
+{
+    if constexpr (G == 4) {
+        const uint4 q = *reinterpret_cast<const uint4*>(p);
+        v[0] = q.x;
+        v[1] = q.y;
+        v[2] = q.z;
+        v[3] = q.w;
+    } else if constexpr (G == 2) {
+        const uint2 q = *reinterpret_cast<const uint2*>(p);
+        v[0] = q.x;
+        v[1] = q.y;
+    } else {
+        v[0] = *p;
+    }
+}
+
+template <int G>
+__device__ __forceinline__ void store_group(uint32_t* p, const uint32_t v[G])
+{
+    if constexpr (G == 4)
+        *reinterpret_cast<uint4*>(p) = make_uint4(v[0], v[1], v[2], v[3]);
+    else if constexpr (G == 2)
+        *reinterpret_cast<uint2*>(p) = make_uint2(v[0], v[1]);
+    else
+        *p = v[0];
+}
+
+// Entries of the per-warp queue of words still undecided after the first two
+// Philox calls: (word position in the tile, undecided sites, flips so far, h = 2
+// sites).  Pushes come 32 at most between drains of 32, so 64 entries suffice.
+constexpr int kQueueCap = 64;
+
+// Per-tile constants of the word update.
+struct TileCtx {
+    const uint32_t* s_src;  // source rows i0 - HB .. i0 + TR + HB - 1 (shared memory)
+    const uint32_t* s_tgt;  // target rows i0 .. i0 + TR - 1 (shared memory)
+    uint32_t* out;          // target plane at row i0 (global memory)
+    uint64_t q_tile;        // Philox call index of the tile's first word: 8 * i0 * W
+    uint64_t key;
+    uint32_t sweep, t2, t4, all2, all4, zero2, zero4;
+    int W, HB, colour;
+    int par0;               // (i0 + colour) & 1: row i0 + r has its horizontal neighbour on the right iff r + par0 is odd
+    bool q_small;           // every call index of the lattice below 2^32
+};
+
+__device__ __forceinline__ PhiloxWordConsts group_consts(const TileCtx& x, const PhiloxWordConsts& pc_tile, uint64_t q)
+{
+    return x.q_small ? pc_tile : philox_consts(x.key, (uint32_t)(q >> 32), x.sweep, (uint32_t)x.colour);
+}
+
+// Calls 2..7 for the top n queue entries, one per lane < n (every lane of the warp
+// takes part), then the words' final values and counts.
+__device__ __forceinline__ void drain_queue(const TileCtx& x, const PhiloxWordConsts& pc_tile, uint4* wq, int& qn,
+                                            int n, int lane, uint32_t& ups, uint32_t& anti)
+{
+    const bool act = lane < n;
+    uint4 e = make_uint4(0u, 0u, 0u, 0u);
+    if (act) e = wq[qn - n + lane];
+    qn -= n;
+    __syncwarp();  // entries read before the next pushes overwrite them
+    uint32_t und[1] = {e.y}, fm[1] = {e.z};
+    const uint32_t sel[1] = {e.w};
+    const uint64_t q = x.q_tile + 8ull * e.x;
+    const uint32_t ql[1] = {(uint32_t)q};
+    const uint32_t thr[2] = {x.t2, x.t4};
+    bitsliced_below<1, 2, 2, 8, true>(und, fm, sel, sel, ql, group_consts(x, pc_tile, q), x.key, thr);
+    if (act) {
+        const uint32_t nw = x.s_tgt[e.x] ^ fm[0];
+        x.out[e.x] = nw;
+        if (x.colour == 1) {
+            ups += __popc(nw);
+            anti += 4u * __popc(fm[0]) - 2u * __popc(fm[0] & sel[0]);
+        }
+    }
+}
+
+// One staged tile of TR rows, G adjacent words per thread and step (G = 4 when
+// W % 4 == 0: one 128-bit shared-memory load per neighbour row).  Every word
+// draws its first two Philox calls (8 bit planes, which decide all of a word's
+// sites with probability about 0.9 at the critical point) in step with its warp;
+// words with sites left wait in the warp's queue, drained 32 at a time with one
+// word per lane.  So the rare long comparisons no longer hold a whole warp, which
+// draws about 2.2 calls per word instead of the ~3.4 a warp-wide early exit needs.
+// A queued word is stored twice: as far as decided, then final (ordered by
+// __syncwarp).  Counts as in flip_masks.
+template <int NT, int G>
+__device__ __forceinline__ void update_tile(const TileCtx& x, const PhiloxWordConsts& pc_tile, int nwords, uint4* wq,
+                                            uint32_t& ups, uint32_t& anti)
+{
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int W = x.W, WG = W / G, ngroups = nwords / G;
+    int qn = 0;  // entries in the warp's queue (the same in every lane)
+    // (row, group) of g = tid + k*NT, advanced without a division
+    const int step_r = NT / WG, step_w = NT - step_r * WG;
+    int r = tid / WG, wg = tid - r * WG;
+    for (int k0 = 0; k0 < ngroups; k0 += NT) {
+        // every lane runs every step (the votes and the queue need the whole warp);
+        // a lane past the end works on group 0 and keeps nothing
+        const bool valid = k0 + tid < ngroups;
+        const int rr = valid ? r : 0, w = valid ? wg * G : 0;
+        const uint32_t* srow = x.s_src + (size_t)(x.HB + rr) * W;
+        uint32_t up[G], dn[G], sm[G], tg[G], hz[G];
+        load_group<G>(srow + w - W, up);
+        load_group<G>(srow + w + W, dn);
+        load_group<G>(srow + w, sm);
+        load_group<G>(x.s_tgt + (size_t)rr * W + w, tg);
+        if ((rr + x.par0) & 1) {
+            const uint32_t next = srow[(w + G == W) ? 0 : w + G];
+#pragma unroll
+            for (int k = 0; k < G; ++k) hz[k] = __funnelshift_r(sm[k], k + 1 < G ? sm[k + 1] : next, 1);
+        } else {
+            const uint32_t prev = srow[(w == 0) ? W - 1 : w - 1];
+#pragma unroll
+            for (int k = 0; k < G; ++k) hz[k] = __funnelshift_l(k > 0 ? sm[k - 1] : prev, sm[k], 1);
+        }
+        const uint32_t pos0 = (uint32_t)(rr * W + w);
+        const uint64_t q0 = x.q_tile + 8ull * pos0;  // the group's calls share q's high word
+        uint32_t und[G], fm[G], sel[G], ql[G];
+#pragma unroll
+        for (int k = 0; k < G; ++k) {
+            uint32_t anti0;
+            classify_word(tg[k], up[k], dn[k], sm[k], hz[k], x.all2, x.all4, x.zero2, x.zero4, fm[k], und[k],
+                          sel[k], anti0);
+            if (!valid) und[k] = 0u;
+            if (x.colour == 1 && valid) {
+                ups += __popc(sm[k]);
+                anti += anti0;
+            }
+            ql[k] = (uint32_t)q0 + 8u * k;
+        }
+        const uint32_t thr[2] = {x.t2, x.t4};
+        bitsliced_below<G, 2, 0, 2, true>(und, fm, sel, sel, ql, group_consts(x, pc_tile, q0), x.key, thr);
+        // the target words again, so that they need not stay in registers above
+        uint32_t nw[G];
+        if constexpr (G == 4) {
+            const uint4 tq = ld_shared_v4(x.s_tgt + (size_t)rr * W + w);
+            nw[0] = tq.x ^ fm[0];
+            nw[1] = tq.y ^ fm[1];
+            nw[2] = tq.z ^ fm[2];
+            nw[3] = tq.w ^ fm[3];
+        } else {
+#pragma unroll
+            for (int k = 0; k < G; ++k) nw[k] = tg[k] ^ fm[k];
+        }
+        if (valid) store_group<G>(x.out + pos0, nw);
+#pragma unroll
+        for (int k = 0; k < G; ++k) {
+            const bool pend = und[k] != 0u;
+            if (x.colour == 1 && valid && !pend) {
+                ups += __popc(nw[k]);
+                anti += 4u * __popc(fm[k]) - 2u * __popc(fm[k] & sel[k]);
+            }
+            const uint32_t bal = __ballot_sync(0xffffffffu, pend);
+            if (pend) wq[qn + __popc(bal & ((1u << lane) - 1u))] = make_uint4(pos0 + k, und[k], fm[k], sel[k]);
+            qn += __popc(bal);
+            if (qn >= 32) {
+                __syncwarp();  // pushes visible to the draining lanes
+                drain_queue(x, pc_tile, wq, qn, 32, lane, ups, anti);
+            }
+        }
+        r += step_r;
+        wg += step_w;
+        if (wg >= WG) {
+            wg -= WG;
+            ++r;
+        }
+    }
+    if (qn > 0) {
+        __syncwarp();
+        drain_queue(x, pc_tile, wq, qn, qn, lane, ups, anti);
+    }
+}
+
 // Register budgets: the single-lattice instance reads its descriptor from a
 // __grid_constant__ parameter, so the key, thresholds and Philox constants sit in
 // uniform registers and 2 CTAs of 256 fit at <= 128 registers; the general instance
@@ -196,7 +373,8 @@ __global__ void __launch_bounds__(NT, (ONE ? (ISING_SWEEP_THREADS_PER_SM / NT > 
     extern __shared__ __align__(128) unsigned char smem_raw[];
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);
     uint32_t* red = reinterpret_cast<uint32_t*>(smem_raw + 16);  // 2 * NT/32 words
-    uint32_t* stages = reinterpret_cast<uint32_t*>(smem_raw + 128 + ((2 * (NT / 32) * 4 + 127) / 128) * 128);
+    uint4* queues = reinterpret_cast<uint4*>(smem_raw + 128 + ((2 * (NT / 32) * 4 + 127) / 128) * 128);
+    uint32_t* stages = reinterpret_cast<uint32_t*>(queues + (NT / 32) * kQueueCap);
     const int tid = threadIdx.x;
     const int count = ONE ? 1 : *tt.count;
     const int total = ONE ? one.L / one.tile_rows : __ldg(tt.tile_start + count);
@@ -294,166 +472,34 @@ __global__ void __launch_bounds__(NT, (ONE ? (ISING_SWEEP_THREADS_PER_SM / NT > 
             }
             // counter words q = i*L/8 + 8w stay below 2^32 when L <= 131072, so the
             // per-word Philox constants (which depend on q's high word) are fixed
-            const bool q_small = L <= 131072;
+            TileCtx x;
+            x.s_src = s_src;
+            x.s_tgt = s_tgt;
+            x.out = out_plane + (size_t)i0 * W;
+            x.q_tile = 8ull * (uint64_t)i0 * (uint64_t)W;
+            x.key = key;
+            x.sweep = sweep;
+            x.t2 = t2;
+            x.t4 = t4;
+            x.all2 = all2;
+            x.all4 = all4;
+            x.zero2 = (t2 == 0u && all2 == 0u) ? ~0u : 0u;  // thresholds 0 (never accept) are
+            x.zero4 = (t4 == 0u && all4 == 0u) ? ~0u : 0u;  // taken out of the test like 2^32
+            x.W = W;
+            x.HB = HB;
+            x.colour = colour;
+            x.par0 = (i0 + colour) & 1;
+            x.q_small = L <= 131072;
             const PhiloxWordConsts pc_tile = philox_consts(key, 0u, sweep, (uint32_t)colour);
+            uint4* wq = queues + (tid >> 5) * kQueueCap;
             const int nwords = TR * W;
-            // Four (or two) adjacent words per thread and iteration: one 128-bit (or
-            // 64-bit) shared-memory load per neighbour row and one global store, and
-            // one index step, per group of words.
-            if ((W & 3) == 0) {
-                const int W4 = W >> 2, nquads = nwords >> 2;
-                const int step_r = NT / W4, step_w = NT - step_r * W4;
-                int r = tid / W4, w4 = tid - r * W4;
-                for (int idx4 = tid; idx4 < nquads; idx4 += NT) {
-                    const int i = i0 + r;
-                    const int w = 4 * w4;
-                    const uint32_t* srow = s_src + (size_t)(HB + r) * W;
-                    const uint4 upq = *reinterpret_cast<const uint4*>(srow + w - W);
-                    const uint4 dnq = *reinterpret_cast<const uint4*>(srow + w + W);
-                    const uint4 smq = *reinterpret_cast<const uint4*>(srow + w);
-                    const uint4 tgq = *reinterpret_cast<const uint4*>(s_tgt + (size_t)r * W + w);
-                    const int par = (i + colour) & 1;
-                    uint32_t hz[4];
-                    if (par) {
-                        const uint32_t nextw = srow[(w + 4 == W) ? 0 : w + 4];
-                        hz[0] = __funnelshift_r(smq.x, smq.y, 1);
-                        hz[1] = __funnelshift_r(smq.y, smq.z, 1);
-                        hz[2] = __funnelshift_r(smq.z, smq.w, 1);
-                        hz[3] = __funnelshift_r(smq.w, nextw, 1);
-                    } else {
-                        const uint32_t prevw = srow[(w == 0) ? W - 1 : w - 1];
-                        hz[0] = __funnelshift_l(prevw, smq.x, 1);
-                        hz[1] = __funnelshift_l(smq.x, smq.y, 1);
-                        hz[2] = __funnelshift_l(smq.y, smq.z, 1);
-                        hz[3] = __funnelshift_l(smq.z, smq.w, 1);
-                    }
-                    const uint64_t q0 = (uint64_t)i * (uint64_t)(L >> 3) + 8ull * (uint64_t)w;
-                    const PhiloxWordConsts pc =
-                        q_small ? pc_tile : philox_consts(key, (uint32_t)(q0 >> 32), sweep, (uint32_t)colour);
-                    const uint32_t up[4] = {upq.x, upq.y, upq.z, upq.w}, dn[4] = {dnq.x, dnq.y, dnq.z, dnq.w};
-                    const uint32_t sm[4] = {smq.x, smq.y, smq.z, smq.w}, tg[4] = {tgq.x, tgq.y, tgq.z, tgq.w};
-                    const uint32_t ql[4] = {(uint32_t)q0, (uint32_t)q0 + 8u, (uint32_t)q0 + 16u, (uint32_t)q0 + 24u};
-                    // the random-number loop runs on two words at a time: a thread stops
-                    // drawing once both are decided, and a warp once all its lanes are, so
-                    // the smaller group draws fewer calls at warp level than all four
-                    // words together would (the pair interleaves two calls)
-                    uint32_t f[4];
-#pragma unroll
-                    for (int hh = 0; hh < 2; ++hh) {
-                        const uint32_t a_t[2] = {tg[2 * hh], tg[2 * hh + 1]}, a_u[2] = {up[2 * hh], up[2 * hh + 1]};
-                        const uint32_t a_d[2] = {dn[2 * hh], dn[2 * hh + 1]}, a_s[2] = {sm[2 * hh], sm[2 * hh + 1]};
-                        const uint32_t a_h[2] = {hz[2 * hh], hz[2 * hh + 1]}, a_q[2] = {ql[2 * hh], ql[2 * hh + 1]};
-                        uint32_t a_f[2];
-                        if (colour == 1)
-                            flip_masks<2, true>(a_t, a_u, a_d, a_s, a_h, a_q, pc, key, t2, t4, all2, all4, a_f, ups, anti);
-                        else
-                            flip_masks<2, false>(a_t, a_u, a_d, a_s, a_h, a_q, pc, key, t2, t4, all2, all4, a_f, ups, anti);
-                        f[2 * hh] = a_f[0];
-                        f[2 * hh + 1] = a_f[1];
-                    }
-                    // the target words again from shared memory, so that they need not
-                    // stay in registers across the random-number loop
-                    const uint4 tq = ld_shared_v4(s_tgt + (size_t)r * W + w);
-                    const uint4 nq = make_uint4(tq.x ^ f[0], tq.y ^ f[1], tq.z ^ f[2], tq.w ^ f[3]);
-                    *reinterpret_cast<uint4*>(out_plane + (size_t)i * W + w) = nq;
-                    if (colour == 1) ups += __popc(nq.x) + __popc(nq.y) + __popc(nq.z) + __popc(nq.w);
-                    r += step_r;
-                    w4 += step_w;
-                    if (w4 >= W4) {
-                        w4 -= W4;
-                        ++r;
-                    }
-                }
-            } else if ((W & 1) == 0) {
-                // pairs of adjacent words (W even but not a multiple of 4)
-                const int W2 = W >> 1, npairs = nwords >> 1;
-                const int step_r = NT / W2, step_w = NT - step_r * W2;
-                int r = tid / W2, w2 = tid - r * W2;
-                for (int idx2 = tid; idx2 < npairs; idx2 += NT) {
-                    const int i = i0 + r;
-                    const int w = 2 * w2;
-                    const uint32_t* srow = s_src + (size_t)(HB + r) * W;
-                    const uint2 upp = *reinterpret_cast<const uint2*>(srow + w - W);
-                    const uint2 dnp = *reinterpret_cast<const uint2*>(srow + w + W);
-                    const uint2 smp = *reinterpret_cast<const uint2*>(srow + w);
-                    const uint2 tgp = *reinterpret_cast<const uint2*>(s_tgt + (size_t)r * W + w);
-                    const int par = (i + colour) & 1;
-                    uint32_t hz0, hz1;
-                    if (par) {
-                        const uint32_t nextw = srow[(w + 2 == W) ? 0 : w + 2];
-                        hz0 = __funnelshift_r(smp.x, smp.y, 1);
-                        hz1 = __funnelshift_r(smp.y, nextw, 1);
-                    } else {
-                        const uint32_t prevw = srow[(w == 0) ? W - 1 : w - 1];
-                        hz0 = __funnelshift_l(prevw, smp.x, 1);
-                        hz1 = __funnelshift_l(smp.x, smp.y, 1);
-                    }
-                    const uint64_t q0 = (uint64_t)i * (uint64_t)(L >> 3) + 8ull * (uint64_t)w;
-                    const PhiloxWordConsts pc =
-                        q_small ? pc_tile : philox_consts(key, (uint32_t)(q0 >> 32), sweep, (uint32_t)colour);
-                    uint32_t f[2];
-                    {
-                        const uint32_t t2w[2] = {tgp.x, tgp.y};
-                        const uint32_t u2[2] = {upp.x, upp.y}, d2[2] = {dnp.x, dnp.y}, m2[2] = {smp.x, smp.y};
-                        const uint32_t z2[2] = {hz0, hz1}, ql[2] = {(uint32_t)q0, (uint32_t)q0 + 8u};
-                        if (colour == 1)
-                            flip_masks<2, true>(t2w, u2, d2, m2, z2, ql, pc, key, t2, t4, all2, all4, f, ups, anti);
-                        else
-                            flip_masks<2, false>(t2w, u2, d2, m2, z2, ql, pc, key, t2, t4, all2, all4, f, ups, anti);
-                    }
-                    const uint2 nw = make_uint2(tgp.x ^ f[0], tgp.y ^ f[1]);
-                    *reinterpret_cast<uint2*>(out_plane + (size_t)i * W + w) = nw;
-                    if (colour == 1) ups += __popc(nw.x) + __popc(nw.y);
-                    r += step_r;
-                    w2 += step_w;
-                    if (w2 >= W2) {
-                        w2 -= W2;
-                        ++r;
-                    }
-                }
-            } else {
-            // (row, word) of idx = tid + k*NT, advanced without a division per word
-            const int step_r = NT / W, step_w = NT - step_r * W;
-            int r = tid / W, w = tid - r * W;
-            for (int idx = tid; idx < nwords; idx += NT) {
-                const int i = i0 + r;
-                const uint32_t* srow = s_src + (size_t)(HB + r) * W;
-                const uint32_t up = srow[w - W];
-                const uint32_t down = srow[w + W];
-                const uint32_t same = srow[w];
-                const int par = (i + colour) & 1;
-                uint32_t hz;
-                if (par) {
-                    const uint32_t nextw = srow[(w + 1 == W) ? 0 : w + 1];
-                    hz = __funnelshift_r(same, nextw, 1);
-                } else {
-                    const uint32_t prevw = srow[(w == 0) ? W - 1 : w - 1];
-                    hz = __funnelshift_l(prevw, same, 1);
-                }
-                const uint32_t tw = s_tgt[idx];
-                const uint64_t q0 = (uint64_t)i * (uint64_t)(L >> 3) + 8ull * (uint64_t)w;
-                const PhiloxWordConsts pc =
-                    q_small ? pc_tile : philox_consts(key, (uint32_t)(q0 >> 32), sweep, (uint32_t)colour);
-                uint32_t f[1];
-                {
-                    const uint32_t t1[1] = {tw};
-                    const uint32_t u1[1] = {up}, d1[1] = {down}, m1[1] = {same}, z1[1] = {hz}, ql[1] = {(uint32_t)q0};
-                    if (colour == 1)
-                        flip_masks<1, true>(t1, u1, d1, m1, z1, ql, pc, key, t2, t4, all2, all4, f, ups, anti);
-                    else
-                        flip_masks<1, false>(t1, u1, d1, m1, z1, ql, pc, key, t2, t4, all2, all4, f, ups, anti);
-                }
-                out_plane[(size_t)i * W + w] = tw ^ f[0];
-                if (colour == 1) ups += __popc(tw ^ f[0]);
-                r += step_r;
-                w += step_w;
-                if (w >= W) {
-                    w -= W;
-                    ++r;
-                }
-            }
+            if ((W & 3) == 0)
+                update_tile<NT, 4>(x, pc_tile, nwords, wq, ups, anti);
+            else if ((W & 1) == 0)
+                update_tile<NT, 2>(x, pc_tile, nwords, wq, ups, anti);
+            else
+                update_tile<NT, 1>(x, pc_tile, nwords, wq, ups, anti);
         }
-            }
         __syncthreads();
         buf ^= 1;
         cur = nxt;
@@ -477,7 +523,7 @@ __global__ void packed_advance_kernel(LatticeDesc* desc, const int32_t* count, i
 
 int packed_smem_header_bytes(int threads)
 {
-    return 128 + ((2 * (threads / 32) * 4 + 127) / 128) * 128;
+    return 128 + ((2 * (threads / 32) * 4 + 127) / 128) * 128 + (threads / 32) * kQueueCap * 16;
 }
 
 template <int NT>

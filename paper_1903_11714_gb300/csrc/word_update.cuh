@@ -23,7 +23,12 @@ namespace ising {
 // threshold (ORed into).  NTH thresholds t[0..NTH-1] (values min(T, 2^32 - 1)); a
 // site's threshold is t[0] where selA, else t[1] where selB (NTH = 3), else the
 // last one.  Sites whose threshold is 0 or 2^32 must not be in und.
-template <int G, int NTH>
+//
+// Calls C0 .. C1-1 (planes 4*C0 .. 4*C1-1) are drawn; sites still in und after
+// call 7 are not below (U equals T).  VOTE: stop when no site of the whole warp is
+// undecided (every lane of the warp must be present), else when none of this
+// thread's is.
+template <int G, int NTH, int C0 = 0, int C1 = 8, bool VOTE = false>
 __device__ __forceinline__ void bitsliced_below(uint32_t und[G], uint32_t lt[G], const uint32_t selA[G],
                                                 const uint32_t selB[G], const uint32_t q_lo[G],
                                                 const PhiloxWordConsts& pc, uint64_t key, const uint32_t (&t)[NTH])
@@ -32,11 +37,11 @@ __device__ __forceinline__ void bitsliced_below(uint32_t und[G], uint32_t lt[G],
 #pragma unroll
     for (int k = 0; k < G; ++k) base[k] = q_lo[k] ^ pc.x0k;
 #pragma unroll
-    for (int c = 0; c < 8; ++c) {
+    for (int c = C0; c < C1; ++c) {
         uint32_t any = 0;
 #pragma unroll
         for (int k = 0; k < G; ++k) any |= und[k];
-        if (any == 0) break;
+        if (VOTE ? !__any_sync(0xffffffffu, any != 0u) : any == 0u) break;
         uint32_t o[G][4];
         philox_calls<G>(base, (uint32_t)c, pc, key, o);
 #pragma unroll
@@ -76,6 +81,31 @@ __device__ __forceinline__ void bitsliced_below(uint32_t und[G], uint32_t lt[G],
 // popc(b0) + 2 popc(b1) + 4 popc(b2) + sum over f of (4 - 2n)
 //   = popc(b0) - 2 popc(b1) - 4 popc(b2) + 4 popc(f) - 2 popc(f & b0).
 // (Unsigned wrap-around is harmless: each thread's total is non-negative.)
+// The two-dimensional word classes of one target word t from its four neighbour
+// words: f = sites that flip without a test (h <= 0, or a threshold of 2^32), und =
+// sites to test against T2 (sel = 1, h = 2) or T4 (sel = 0, h = 4), zero2/zero4 =
+// ~0u for a threshold of 0 (never accept).  anti0 = popc(b0) - 2 popc(b1) -
+// 4 popc(b2), the update-independent part of the bond count (see flip_masks).
+__device__ __forceinline__ void classify_word(uint32_t t, uint32_t up, uint32_t down, uint32_t same, uint32_t hz,
+                                              uint32_t all2, uint32_t all4, uint32_t zero2, uint32_t zero4,
+                                              uint32_t& f, uint32_t& und, uint32_t& sel, uint32_t& anti0)
+{
+    // anti-aligned neighbour bits and their 4-input sum n = 4*b2 + 2*b1 + b0
+    const uint32_t au = t ^ up, ad = t ^ down, as = t ^ same, ah = t ^ hz;
+    const uint32_t s0 = au ^ ad, c0 = au & ad;
+    const uint32_t s1 = as ^ ah, c1 = as & ah;
+    const uint32_t b0 = s0 ^ s1, cc = s0 & s1;
+    const uint32_t b1 = c0 ^ c1 ^ cc;
+    const uint32_t b2 = c0 & c1;
+    // n >= 2 (h <= 0): always; n == 1 (h = 2): U < T2; n == 0 (h = 4): U < T4
+    const uint32_t always = b1 | b2;
+    const uint32_t h2 = b0 & ~always, h4 = ~b0 & ~always;
+    f = always | (h2 & all2) | (h4 & all4);
+    und = (h2 & ~(all2 | zero2)) | (h4 & ~(all4 | zero4));
+    sel = b0;
+    anti0 = __popc(b0) - 2u * __popc(b1) - 4u * __popc(b2);
+}
+
 template <int G, bool COUNT>
 __device__ __forceinline__ void flip_masks(const uint32_t t[G], const uint32_t up[G], const uint32_t down[G],
                                            const uint32_t same[G], const uint32_t hz[G], const uint32_t q_lo[G],
@@ -88,22 +118,11 @@ __device__ __forceinline__ void flip_masks(const uint32_t t[G], const uint32_t u
     uint32_t und[G], sel[G];
 #pragma unroll
     for (int k = 0; k < G; ++k) {
-        // anti-aligned neighbour bits and their 4-input sum n = 4*b2 + 2*b1 + b0
-        const uint32_t au = t[k] ^ up[k], ad = t[k] ^ down[k], as = t[k] ^ same[k], ah = t[k] ^ hz[k];
-        const uint32_t s0 = au ^ ad, c0 = au & ad;
-        const uint32_t s1 = as ^ ah, c1 = as & ah;
-        const uint32_t b0 = s0 ^ s1, cc = s0 & s1;
-        const uint32_t b1 = c0 ^ c1 ^ cc;
-        const uint32_t b2 = c0 & c1;
-        // n >= 2 (h <= 0): always; n == 1 (h = 2): U < T2; n == 0 (h = 4): U < T4
-        const uint32_t always = b1 | b2;
-        const uint32_t h2 = b0 & ~always, h4 = ~b0 & ~always;
-        f[k] = always | (h2 & all2) | (h4 & all4);
-        und[k] = (h2 & ~(all2 | zero2)) | (h4 & ~(all4 | zero4));
-        sel[k] = b0;
+        uint32_t anti0;
+        classify_word(t[k], up[k], down[k], same[k], hz[k], all2, all4, zero2, zero4, f[k], und[k], sel[k], anti0);
         if (COUNT) {
             ups += __popc(same[k]);
-            anti += __popc(b0) - 2u * __popc(b1) - 4u * __popc(b2);
+            anti += anti0;
         }
     }
     bitsliced_below<G, 2>(und, f, sel, sel, q_lo, pc, key, thr);
