@@ -11,7 +11,8 @@
 //
 // GB300 mapping: a persistent grid (two 256-thread CTAs per SM) walks groups of
 // four adjacent words (one 16-byte vector load per neighbour row through the
-// read-only path; 128 sites per thread iteration).  The kernel is bound by the
+// read-only path; 128 sites per thread iteration); words still undecided after
+// two Philox calls finish from a per-warp queue in shared memory.  The kernel is bound by the
 // integer pipes (Philox), not by memory: a half-sweep moves 3/16 byte per
 // updated site, and the six neighbour rows of a word are re-read from L2.
 #include <cstdint>
@@ -25,61 +26,75 @@ namespace {
 
 constexpr int kThreads3 = 256;
 
-// New values of G adjacent 32-site target words t[k] (in place) from their six
-// neighbour words; q_lo[k] = 8 * (plane word index) of word k.  With COUNT, adds
-// the fused observables as in 2D (word_update.cuh): ups += set bits of the new
-// target and the `same` source words; anti += anti-aligned bonds after the update,
-// from the adder bits: a site with n anti-aligned neighbours has n if it stays and
-// 6 - n if it flips.  Sites with n >= 3 always flip, so the sum over the flip mask
-// f of (6 - 2n) needs, besides popc(f), only the tested classes n = 1 (b0 alone)
-// and n = 2 (b1 alone) among the flipped sites.
-template <int G, bool COUNT>
-__device__ __forceinline__ void update_words3d(uint32_t t[G], const uint32_t up[G], const uint32_t dn[G],
-                                               const uint32_t no[G], const uint32_t so[G], const uint32_t same[G],
-                                               const uint32_t hz[G], const uint32_t q_lo[G],
-                                               const PhiloxWordConsts& pc, const CubicDesc& d, uint32_t& ups,
-                                               uint32_t& anti)
+// Classes of one 32-site target word t from its six neighbour words: f = sites
+// that flip without a test (h <= 0, or a threshold of 2^32), und = sites to test
+// against T2 (selA, h = 2), T4 (selB, h = 4) or T6 (the rest, h = 6); zeroN = ~0u
+// for a threshold of 0 (never accept).  The fused observables come from the adder
+// bits as in 2D (word_update.cuh): a site with n anti-aligned neighbours has n if
+// it stays and 6 - n if it flips.  Sites with n >= 3 always flip, so anti0 = the
+// sum of n minus the always-flipped sites' 2 (b0) + 4 (b1) + 8 (b2) parts, and
+// once the word is decided the flip mask f adds 6 popc(f) - 2 popc(f & selB) -
+// 4 popc(f & selA) (the tested classes n = 1 and n = 2 among the flipped sites).
+__device__ __forceinline__ void classify_word3d(uint32_t t, uint32_t up, uint32_t dn, uint32_t no, uint32_t so,
+                                                uint32_t same, uint32_t hz, const CubicDesc& d, uint32_t zero2,
+                                                uint32_t zero4, uint32_t zero6, uint32_t& f, uint32_t& und,
+                                                uint32_t& selA, uint32_t& selB, uint32_t& anti0)
 {
-    const uint32_t thr[3] = {d.t2, d.t4, d.t6};
-    const uint32_t zero2 = (d.t2 == 0u && d.all2 == 0u) ? ~0u : 0u;
-    const uint32_t zero4 = (d.t4 == 0u && d.all4 == 0u) ? ~0u : 0u;
-    const uint32_t zero6 = (d.t6 == 0u && d.all6 == 0u) ? ~0u : 0u;
-    uint32_t always[G], und[G], lt[G], selA[G], selB[G];
-#pragma unroll
-    for (int k = 0; k < G; ++k) {
-        // anti-aligned neighbour bits and their 6-input sum n = 4*b2 + 2*b1 + b0:
-        // two full adders over three inputs each, then the sum bits added (b0,
-        // carry c3) and the three weight-2 carries added (b1, b2)
-        const uint32_t a0 = t[k] ^ up[k], a1 = t[k] ^ dn[k], a2 = t[k] ^ no[k];
-        const uint32_t a3 = t[k] ^ so[k], a4 = t[k] ^ same[k], a5 = t[k] ^ hz[k];
-        const uint32_t s1 = a0 ^ a1 ^ a2, c1 = (a0 & a1) | (a2 & (a0 ^ a1));
-        const uint32_t s2 = a3 ^ a4 ^ a5, c2 = (a3 & a4) | (a5 & (a3 ^ a4));
-        const uint32_t b0 = s1 ^ s2, c3 = s1 & s2;
-        const uint32_t b1 = c1 ^ c2 ^ c3;
-        const uint32_t b2 = (c1 & c2) | (c3 & (c1 ^ c2));
-        // h = 6 - 2n: n >= 3 (h <= 0) always; n = 2 (h = 2): U < T2; n = 1 (h = 4):
-        // U < T4; n = 0 (h = 6): U < T6
-        always[k] = b2 | (b1 & b0);
-        const uint32_t h2 = b1 & ~b0 & ~b2, h4 = b0 & ~b1 & ~b2, h6 = ~(b0 | b1 | b2);
-        lt[k] = (h2 & d.all2) | (h4 & d.all4) | (h6 & d.all6);
-        und[k] = (h2 & ~(d.all2 | zero2)) | (h4 & ~(d.all4 | zero4)) | (h6 & ~(d.all6 | zero6));
-        selA[k] = h2;
-        selB[k] = h4;
-        if (COUNT) {
-            // sum of n, minus the always-flipped sites' 2 (b0) + 4 (b1) + 8 (b2) parts
-            ups += __popc(same[k]);
-            anti += __popc(b0) + 2u * __popc(b1) - 4u * __popc(b2) - 2u * __popc(b0 & (b1 | b2)) -
-                    4u * __popc(b1 & (b0 | b2));
-        }
+    // anti-aligned neighbour bits and their 6-input sum n = 4*b2 + 2*b1 + b0: two
+    // full adders over three inputs each, then the sum bits added (b0, carry c3)
+    // and the three weight-2 carries added (b1, b2)
+    const uint32_t a0 = t ^ up, a1 = t ^ dn, a2 = t ^ no;
+    const uint32_t a3 = t ^ so, a4 = t ^ same, a5 = t ^ hz;
+    const uint32_t s1 = a0 ^ a1 ^ a2, c1 = (a0 & a1) | (a2 & (a0 ^ a1));
+    const uint32_t s2 = a3 ^ a4 ^ a5, c2 = (a3 & a4) | (a5 & (a3 ^ a4));
+    const uint32_t b0 = s1 ^ s2, c3 = s1 & s2;
+    const uint32_t b1 = c1 ^ c2 ^ c3;
+    const uint32_t b2 = (c1 & c2) | (c3 & (c1 ^ c2));
+    // h = 6 - 2n: n >= 3 (h <= 0) always; n = 2 (h = 2): U < T2; n = 1 (h = 4):
+    // U < T4; n = 0 (h = 6): U < T6
+    const uint32_t always = b2 | (b1 & b0);
+    const uint32_t h2 = b1 & ~b0 & ~b2, h4 = b0 & ~b1 & ~b2, h6 = ~(b0 | b1 | b2);
+    f = always | (h2 & d.all2) | (h4 & d.all4) | (h6 & d.all6);
+    und = (h2 & ~(d.all2 | zero2)) | (h4 & ~(d.all4 | zero4)) | (h6 & ~(d.all6 | zero6));
+    selA = h2;
+    selB = h4;
+    anti0 = __popc(b0) + 2u * __popc(b1) - 4u * __popc(b2) - 2u * __popc(b0 & (b1 | b2)) - 4u * __popc(b1 & (b0 | b2));
+}
+
+// Words still undecided after the first two Philox calls wait in a per-warp queue;
+// an entry is two 16-byte slots: (position low, position high, undecided sites,
+// flips so far) and (h = 2 sites, h = 4 sites, old target word, unused).  Pushes
+// come 32 at most between drains of 32, so 64 entries suffice.
+constexpr int kQueueCap3 = 64;
+
+// Calls 2..7 for the top n queue entries, one per lane < n (every lane of the warp
+// takes part), then the words' final values and counts.
+__device__ __forceinline__ void drain_queue3d(const CubicDesc& d, uint32_t* tgt, const PhiloxWordConsts& pc_all,
+                                              bool q_small, int colour, uint32_t sweep, uint4* wq, int& qn, int n,
+                                              int lane, uint32_t& ups, uint32_t& anti)
+{
+    const bool act = lane < n;
+    uint4 e0 = make_uint4(0u, 0u, 0u, 0u), e1 = make_uint4(0u, 0u, 0u, 0u);
+    if (act) {
+        e0 = wq[2 * (qn - n + lane)];
+        e1 = wq[2 * (qn - n + lane) + 1];
     }
-    bitsliced_below<G, 3>(und, lt, selA, selB, q_lo, pc, d.key, thr);
-#pragma unroll
-    for (int k = 0; k < G; ++k) {
-        const uint32_t f = always[k] | lt[k];
-        t[k] ^= f;
-        if (COUNT) {
-            ups += __popc(t[k]);
-            anti += 6u * __popc(f) - 2u * __popc(lt[k] & selB[k]) - 4u * __popc(lt[k] & selA[k]);
+    qn -= n;
+    __syncwarp();  // entries read before the next pushes overwrite them
+    const uint64_t pos = (uint64_t)e0.x | ((uint64_t)e0.y << 32);
+    uint32_t und[1] = {e0.z}, f[1] = {e0.w};
+    const uint32_t selA[1] = {e1.x}, selB[1] = {e1.y};
+    const uint64_t q = 8ull * pos;
+    const uint32_t ql[1] = {(uint32_t)q};
+    const PhiloxWordConsts pc = q_small ? pc_all : philox_consts(d.key, (uint32_t)(q >> 32), sweep, (uint32_t)colour);
+    const uint32_t thr[3] = {d.t2, d.t4, d.t6};
+    bitsliced_below<1, 3, 2, 8, true>(und, f, selA, selB, ql, pc, d.key, thr);
+    if (act) {
+        const uint32_t nw = e1.z ^ f[0];
+        tgt[pos] = nw;
+        if (colour == 1) {
+            ups += __popc(nw);
+            anti += 6u * __popc(f[0]) - 2u * __popc(f[0] & selB[0]) - 4u * __popc(f[0] & selA[0]);
         }
     }
 }
@@ -180,16 +195,24 @@ __device__ __forceinline__ void block_add_twice(unsigned long long a, unsigned l
     }
 }
 
+// Each word draws its first two Philox calls (8 bit planes) in step with its warp;
+// words with sites left wait in the warp's queue and are finished 32 at a time,
+// one per lane (the 2D tile routine does the same).  A queued word is stored twice:
+// as far as decided, then final (ordered by __syncwarp).
 template <int NT, int G>
 __global__ void __launch_bounds__(NT, 2) cubic_half_sweep_kernel(const __grid_constant__ CubicDesc d, int colour,
                                                                  uint32_t sweep)
 {
     __shared__ unsigned long long red[2 * (NT / 32)];
+    __shared__ uint4 queues[(NT / 32) * 2 * kQueueCap3];
     const int64_t L = d.L;
     const int W = d.W, WG = W / G;
     const int64_t ngroups = L * L * WG;
     const uint32_t* __restrict__ src = d.plane[colour ^ 1];
     uint32_t* __restrict__ tgt = d.plane[colour];
+    const int lane = threadIdx.x & 31;
+    uint4* wq = queues + (threadIdx.x >> 5) * 2 * kQueueCap3;
+    int qn = 0;  // entries in the warp's queue (the same in every lane)
     if (colour == 0 && blockIdx.x == 0 && threadIdx.x == 0) {
         // open this sweep's (M, E) slot: M = 2 * ups - N, E = 2 * anti - 3N
         const int64_t N = L * L * L;
@@ -198,8 +221,13 @@ __global__ void __launch_bounds__(NT, 2) cubic_half_sweep_kernel(const __grid_co
     }
     const bool q_small = cubic_q_small(L);
     const PhiloxWordConsts pc_all = philox_consts(d.key, 0u, sweep, (uint32_t)colour);
-    // per-thread counts stay below 2^32: a thread sees at most L^3 / (2 * 152 * 2 * 256)
-    // white sites (< 4e6 at L = 8192) with at most 7 counted bits each
+    const uint32_t zero2 = (d.t2 == 0u && d.all2 == 0u) ? ~0u : 0u;
+    const uint32_t zero4 = (d.t4 == 0u && d.all4 == 0u) ? ~0u : 0u;
+    const uint32_t zero6 = (d.t6 == 0u && d.all6 == 0u) ? ~0u : 0u;
+    const uint32_t thr[3] = {d.t2, d.t4, d.t6};
+    // per-thread counts stay below 2^31 in magnitude: even a whole warp sees at most
+    // L^3 / (2 * 152 * 2 * 8) white sites (< 1.2e8 at L = 8192) with at most 7
+    // counted bits each
     uint32_t ups = 0, anti = 0;
     // (i, j, word group) of g = start + k * stride, advanced without divisions: the
     // stride is step_w groups within a row plus step_r rows, step_r = step_i * L + step_j
@@ -221,14 +249,18 @@ __global__ void __launch_bounds__(NT, 2) cubic_half_sweep_kernel(const __grid_co
     const int64_t Wl = W, LW = L * Wl, LLW = L * LW;
     const int64_t step_off = step_r * Wl;
     int64_t row = (i * L + j) * Wl;
-    for (int64_t g = start; g < ngroups; g += stride) {
-        const int w = wg * G;
-        const int par = (int)((i + j + colour) & 1);
-        const int64_t up = row + (i == 0 ? LLW - LW : -LW), dn = row + (i == L - 1 ? LW - LLW : LW);
-        const int64_t no = row + (j == 0 ? LW - Wl : -Wl), so = row + (j == L - 1 ? Wl - LW : Wl);
+    // every lane runs every step (the votes and the queue need the whole warp); a
+    // lane past the end works on group 0 and keeps nothing
+    for (int64_t g0 = start - lane; g0 < ngroups; g0 += stride) {
+        const bool valid = g0 + lane < ngroups;
+        const int64_t vi = valid ? i : 0, vj = valid ? j : 0, vrow = valid ? row : 0;
+        const int w = valid ? wg * G : 0;
+        const int par = (int)((vi + vj + colour) & 1);
+        const int64_t up = vrow + (vi == 0 ? LLW - LW : -LW), dn = vrow + (vi == L - 1 ? LW - LLW : LW);
+        const int64_t no = vrow + (vj == 0 ? LW - Wl : -Wl), so = vrow + (vj == L - 1 ? Wl - LW : Wl);
         Nbr<G> n;
-        load_neighbours_at<G>(src, W, row, up, dn, no, so, w, par, n);
-        uint32_t* trow = tgt + row + w;
+        load_neighbours_at<G>(src, W, vrow, up, dn, no, so, w, par, n);
+        uint32_t* trow = tgt + vrow + w;
         uint32_t t[G];
         if constexpr (G == 4) {
             const uint4 q = *reinterpret_cast<const uint4*>(trow);
@@ -242,24 +274,53 @@ __global__ void __launch_bounds__(NT, 2) cubic_half_sweep_kernel(const __grid_co
         }
         // q0 = r * (L/8) + 8w = 8 * (row + w) with L/8 = 8W; it is a multiple of 8 * G,
         // so the group's calls q0 .. q0 + 8G - 1 share q's high word
-        const uint64_t q0 = 8ull * (uint64_t)(row + w);
+        const uint64_t q0 = 8ull * (uint64_t)(vrow + w);
         const PhiloxWordConsts pc =
             q_small ? pc_all : philox_consts(d.key, (uint32_t)(q0 >> 32), sweep, (uint32_t)colour);
-        uint32_t nw[G], ql[G];
+        uint32_t f[G], und[G], selA[G], selB[G], ql[G];
 #pragma unroll
         for (int k = 0; k < G; ++k) {
-            nw[k] = t[k];
+            uint32_t anti0;
+            classify_word3d(t[k], n.up[k], n.dn[k], n.no[k], n.so[k], n.sm[k], n.hz[k], d, zero2, zero4, zero6, f[k],
+                            und[k], selA[k], selB[k], anti0);
+            if (!valid) und[k] = 0u;
+            if (colour == 1 && valid) {
+                ups += __popc(n.sm[k]);
+                anti += anti0;
+            }
             ql[k] = (uint32_t)q0 + 8u * k;
         }
-        if (colour == 1)
-            update_words3d<G, true>(nw, n.up, n.dn, n.no, n.so, n.sm, n.hz, ql, pc, d, ups, anti);
-        else
-            update_words3d<G, false>(nw, n.up, n.dn, n.no, n.so, n.sm, n.hz, ql, pc, d, ups, anti);
-        if constexpr (G == 4) {
-            *reinterpret_cast<uint4*>(trow) = make_uint4(nw[0], nw[1], nw[2], nw[3]);
-        } else {
+        bitsliced_below<G, 3, 0, 2, true>(und, f, selA, selB, ql, pc, d.key, thr);
+        uint32_t nw[G];
 #pragma unroll
-            for (int k = 0; k < G; ++k) trow[k] = nw[k];
+        for (int k = 0; k < G; ++k) nw[k] = t[k] ^ f[k];
+        if (valid) {
+            if constexpr (G == 4) {
+                *reinterpret_cast<uint4*>(trow) = make_uint4(nw[0], nw[1], nw[2], nw[3]);
+            } else {
+#pragma unroll
+                for (int k = 0; k < G; ++k) trow[k] = nw[k];
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < G; ++k) {
+            const bool pend = und[k] != 0u;
+            if (colour == 1 && valid && !pend) {
+                ups += __popc(nw[k]);
+                anti += 6u * __popc(f[k]) - 2u * __popc(f[k] & selB[k]) - 4u * __popc(f[k] & selA[k]);
+            }
+            const uint32_t bal = __ballot_sync(0xffffffffu, pend);
+            if (pend) {
+                const int slot = qn + __popc(bal & ((1u << lane) - 1u));
+                const uint64_t pos = (uint64_t)(vrow + w + k);
+                wq[2 * slot] = make_uint4((uint32_t)pos, (uint32_t)(pos >> 32), und[k], f[k]);
+                wq[2 * slot + 1] = make_uint4(selA[k], selB[k], t[k], 0u);
+            }
+            qn += __popc(bal);
+            if (qn >= 32) {
+                __syncwarp();  // pushes visible to the draining lanes
+                drain_queue3d(d, tgt, pc_all, q_small, colour, sweep, wq, qn, 32, lane, ups, anti);
+            }
         }
         wg += step_w;
         j += step_j;
@@ -275,7 +336,15 @@ __global__ void __launch_bounds__(NT, 2) cubic_half_sweep_kernel(const __grid_co
             ++i;
         }
     }
-    if (colour == 1) block_add_twice<NT>(ups, anti, red, d.hist + 2 * (int64_t)sweep);
+    if (qn > 0) {
+        __syncwarp();
+        drain_queue3d(d, tgt, pc_all, q_small, colour, sweep, wq, qn, qn, lane, ups, anti);
+    }
+    // a lane's bond count may be negative (a word's negative part can be added by
+    // the lane that queued it and the rest by the lane that drained it), so it is
+    // widened as a signed value; the block's total is not negative
+    if (colour == 1)
+        block_add_twice<NT>(ups, (unsigned long long)(long long)(int32_t)anti, red, d.hist + 2 * (int64_t)sweep);
 }
 
 // (M, E) of a state: every bond joins a black and a white site, so counting the
