@@ -90,8 +90,9 @@ int ising_thresholds(double beta, uint64_t T[2]);
 int ising_init(ising_t *out, int64_t L, double beta, uint64_t seed);
 
 /*
- * start: ISING_HOT or ISING_COLD.  kernel: ISING_PACKED (L % 64 == 0, 64 <= L <=
- * 1048576) or ISING_INT8 (L % 8 == 0, 8 <= L <= 131072).  stream: a cudaStream_t
+ * start: ISING_HOT or ISING_COLD.  kernel: ISING_PACKED (L % 64 == 0, 64 <= L, and
+ * a double-buffered row tile must fit one 100 KB shared-memory stage: L <= 272896
+ * when L % 256 == 0, else L <= 102336) or ISING_INT8 (L % 8 == 0, 8 <= L <= 131072).  stream: a cudaStream_t
  * on which all of this handle's work is enqueued (the caller keeps it alive
  * until ising_free); NULL makes the handle create and own a non-blocking stream.  Device memory: packed L*L/8
  * bytes, int8 L*L bytes, plus 16 bytes of history per sweep (grown on demand).
@@ -209,7 +210,8 @@ int ising_batch_create(ising_batch_t *out, int32_t capacity, int64_t max_L, int6
                        void *stream);
 
 /*
- * Adds a packed lattice (L % 64 == 0, L <= max_L) that will run `sweeps`
+ * Adds a packed lattice (L % 64 == 0, L <= max_L, and within the sizes
+ * ising_init_ex accepts for ISING_PACKED) that will run `sweeps`
  * sweeps at most (its history capacity).  tile_rows: rows per tile (a power of
  * two from 4 to 256 dividing L, or 2 when L % 256 == 0, whose shared-memory stage
  * fits in 100 KB; 0 = built-in choice).
@@ -288,7 +290,8 @@ int ising_dev_philox(uint64_t key, const uint32_t ctr[4], int64_t nblocks, uint3
  * count lattices (1 <= count <= 64; more is ISING_EINVAL).  For lattice k:
  * black[k], white[k] are device pointers to its two bit planes in the layout of
  * ising_get_planes (L[k]*L[k]/64 uint32 words each, updated in place); L[k] %
- * 64 == 0, 64 <= L[k] <= 2^20; beta[k] finite and >= 0; seed[k] its Philox key;
+ * 64 == 0, 64 <= L[k], L[k] <= 163840 when L[k] % 256 == 0 and L[k] <= 102336
+ * otherwise (4-row tiles must fit a 100 KB stage); beta[k] finite and >= 0; seed[k] its Philox key;
  * me[k] a device array of 2*nsweeps int64 that receives (M, E) after each of the
  * sweeps first_sweep .. first_sweep+nsweeps-1 (M at [2s], E at [2s+1], s counted
  * from first_sweep).  The host arrays black, white, L, beta, seed, me are read

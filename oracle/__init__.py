@@ -110,6 +110,9 @@ def lib():
             L.oracle3d_run.argtypes = [i8p] + dims + [ctypes.c_double, ctypes.c_uint64, ctypes.c_int64,
                                                       ctypes.c_int64, i64p, i64p, ctypes.c_int]
             L.oracle3d_run.restype = ctypes.c_int64
+            L.oracle3d_window.argtypes = dims + [ctypes.c_double, ctypes.c_uint64, ctypes.c_int, ctypes.c_int64,
+                                                 ctypes.c_int64] + [ctypes.c_int64] * 6 + [i8p]
+            L.oracle3d_window.restype = ctypes.c_int
             _lib = L
     return _lib
 
@@ -313,6 +316,19 @@ def run3d(dims, beta: float, seed: int, start: int = HOT, sweeps: int = 1, sweep
     mism = lib().oracle3d_run(_ptr(s, ctypes.c_int8), X, Y, Z, float(beta), int(seed), int(sweep0), int(sweeps),
                               _ptr(M, ctypes.c_int64), _ptr(E, ctypes.c_int64), 1 if check else 0)
     return s, M, E, int(mism)
+
+
+def window3d(dims, beta: float, seed: int, start: int, sweeps: int, origin, shape, sweep0: int = 0) -> np.ndarray:
+    """Exact box of the 3D state after `sweeps` sweeps: shape (h, w, d) from origin
+    (i0, j0, k0), torus-wrapped, index [a, b, c] = site (i0 + a, j0 + b, k0 + c)."""
+    X, Y, Z = _check_dims(dims)
+    h, w, d = (int(v) for v in shape)
+    out = np.empty((h, w, d), dtype=np.int8)
+    rc = lib().oracle3d_window(X, Y, Z, float(beta), int(seed), int(start), int(sweep0), int(sweeps),
+                               *(int(v) for v in origin), h, w, d, _ptr(out, ctypes.c_int8))
+    if rc != 0:
+        raise MemoryError("oracle window buffer")
+    return out
 
 
 def _check_L(L: int) -> None:

@@ -176,6 +176,67 @@ ORACLE_API int64_t oracle3d_half_sweep_words(int8_t *s, int64_t X, int64_t Y, in
     return half_sweep3d(s, X, Y, Z, c, T, 0, 0, words);
 }
 
+/* Exact h x w x d box (origin (i0, j0, k0), torus-wrapped) of the state after
+ * sweeps sweep0 .. sweep0+nsweeps-1 from the start state, without the full lattice:
+ * a site after one half-sweep depends only on itself and its six neighbours, so the
+ * box grown by R = 2 nsweeps in every direction holds all that the box depends on.
+ * Each half-sweep updates the sites of its colour whose neighbours are still exact
+ * and shrinks the exact region by one; the uniforms are those of the sites' global
+ * plane indices.  The grown box may exceed the torus: wrapped copies of a site then
+ * evolve identically.  Returns -1 if the buffer cannot be had. */
+ORACLE_API int oracle3d_window(int64_t X, int64_t Y, int64_t Z, double beta, uint64_t seed, int start,
+                               int64_t sweep0, int64_t nsweeps, int64_t i0, int64_t j0, int64_t k0, int64_t h,
+                               int64_t w, int64_t d, int8_t *out)
+{
+    uint64_t T[3];
+    oracle3d_thresholds(beta, T);
+    const int64_t R = 2 * nsweeps;
+    const int64_t A = h + 2 * R, B = w + 2 * R, C = d + 2 * R;
+    int8_t *buf = (int8_t *)malloc((size_t)(A * B * C));
+    if (!buf) return -1;
+#define BOX(a, b, c) buf[((a) * B + (b)) * C + (c)]
+#pragma omp parallel for schedule(static) if (A * B * C >= 32768)
+    for (int64_t a = 0; a < A; ++a)
+        for (int64_t b = 0; b < B; ++b) {
+            struct word_cache3 wc[2] = {{UINT64_MAX, {0}}, {UINT64_MAX, {0}}};
+            for (int64_t c = 0; c < C; ++c) {
+                int64_t gi = wrap3(i0 - R + a, X), gj = wrap3(j0 - R + b, Y), gk = wrap3(k0 - R + c, Z);
+                if (start == 1) {
+                    BOX(a, b, c) = 1;
+                } else {
+                    int col = (int)((gi + gj + gk) & 1);
+                    uint32_t x = cached_uniform3(&wc[col], plane_index3(Y, Z, gi, gj, gk), seed, 0xFFFFFFFFu, col);
+                    BOX(a, b, c) = (x < 0x80000000u) ? 1 : -1;
+                }
+            }
+        }
+    for (int64_t t = 0; t < 2 * nsweeps; ++t) {
+        uint32_t sweep = (uint32_t)(sweep0 + t / 2);
+        int col = (int)(t & 1);
+        int64_t lo = t + 1;
+#pragma omp parallel for schedule(static) if (A * B * C >= 32768)
+        for (int64_t a = lo; a < A - lo; ++a)
+            for (int64_t b = lo; b < B - lo; ++b) {
+                struct word_cache3 wc = {UINT64_MAX, {0}};
+                for (int64_t c = lo; c < C - lo; ++c) {
+                    int64_t gi = wrap3(i0 - R + a, X), gj = wrap3(j0 - R + b, Y), gk = wrap3(k0 - R + c, Z);
+                    if (((gi + gj + gk) & 1) != col) continue;
+                    int nn = BOX(a - 1, b, c) + BOX(a + 1, b, c) + BOX(a, b - 1, c) + BOX(a, b + 1, c) +
+                             BOX(a, b, c - 1) + BOX(a, b, c + 1);
+                    int hh = BOX(a, b, c) * nn;
+                    uint32_t x = cached_uniform3(&wc, plane_index3(Y, Z, gi, gj, gk), seed, sweep, col);
+                    if (oracle3d_accept(hh, x, T)) BOX(a, b, c) = (int8_t)(-BOX(a, b, c));
+                }
+            }
+    }
+    for (int64_t a = 0; a < h; ++a)
+        for (int64_t b = 0; b < w; ++b)
+            for (int64_t c = 0; c < d; ++c) out[(a * w + b) * d + c] = BOX(a + R, b + R, c + R);
+#undef BOX
+    free(buf);
+    return 0;
+}
+
 /* Sweeps sweep0 .. sweep0+nsweeps-1 (black then white) on s; M[k], E[k] after
  * each sweep when non-NULL.  check != 0 also carries E incrementally and compares
  * it with the recomputed value after every half-sweep; returns the mismatches. */

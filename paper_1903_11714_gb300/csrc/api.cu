@@ -47,7 +47,9 @@ int cuda_fail(cudaError_t e, const char* what)
         if (e_ != cudaSuccess) return cuda_fail(e_, #call);    \
     } while (0)
 
-constexpr int64_t kPackedMaxL = 1 << 20;
+// Largest packed side: a double-buffered tile of 2 rows (plus 1-row halos) must fit
+// in one 100 KB stage, i.e. W = L/64 <= 4264 (see packed_L_ok for other W).
+constexpr int64_t kPackedMaxL = 272896;
 constexpr int64_t kInt8MaxL = 1 << 17;
 constexpr uint32_t kNoTarget = 0xFFFFFFFFu;
 constexpr int64_t kMaxSweeps = 0xFFFFFFFEll;  // sweep counter is a 32-bit Philox counter word
@@ -98,6 +100,17 @@ bool tile_rows_ok(int64_t L, int tr)
     const bool pow2 = tr >= 2 && tr <= kMaxTileRows && (tr & (tr - 1)) == 0;
     return pow2 && (tr >= 4 || (L / 64) % 4 == 0) && tr <= L && L % tr == 0 &&
            stage_bytes_for(L, tr) <= kStageCapBytes;
+}
+
+// A packed side the tiled kernel can sweep: L % 64 == 0, 64 <= L, and some tile height
+// fits a stage -- L <= 272,896 when L % 256 == 0 (2-row tiles, 1-row halos), else
+// L <= 102,336 (4-row tiles with 4-row halos).
+bool packed_L_ok(int64_t L)
+{
+    if (L < 64 || L % 64 || L > kPackedMaxL) return false;
+    for (int tr = 2; tr <= kMaxTileRows; tr <<= 1)
+        if (tile_rows_ok(L, tr)) return true;
+    return false;
 }
 
 // Built-in tile height: about ISING_TILE_WORDS words per tile and at most 64 rows.
@@ -587,8 +600,9 @@ int ising_init_ex(ising_t* out, int64_t L, double beta, uint64_t seed, int start
     if (!thresholds(beta, T)) return fail(ISING_EINVAL, "beta must be finite and >= 0");
     if (start != ISING_HOT && start != ISING_COLD) return fail(ISING_EINVAL, "start must be ISING_HOT or ISING_COLD");
     if (kernel == ISING_PACKED) {
-        if (L < 64 || L % 64 || L > kPackedMaxL)
-            return fail(ISING_EINVAL, "packed kernel needs L %% 64 == 0 and 64 <= L <= %lld", (long long)kPackedMaxL);
+        if (!packed_L_ok(L))
+            return fail(ISING_EINVAL,
+                        "packed kernel needs L %% 64 == 0, 64 <= L, and L <= 272896 (L %% 256 == 0) or L <= 102336");
     } else if (kernel == ISING_INT8) {
         if (L < 8 || L % 8 || L > kInt8MaxL)
             return fail(ISING_EINVAL, "int8 kernel needs L %% 8 == 0 and 8 <= L <= %lld", (long long)kInt8MaxL);
@@ -1087,6 +1101,7 @@ int ising_batch_add(ising_batch_t b, int64_t L, double beta, uint64_t seed, int3
     uint64_t T[2];
     if (!thresholds(beta, T)) return fail(ISING_EINVAL, "beta must be finite and >= 0");
     if (L < 64 || L % 64 || L > b->max_L) return fail(ISING_EINVAL, "L must be a multiple of 64 and <= max_L");
+    if (!packed_L_ok(L)) return fail(ISING_EINVAL, "no tile of L = %lld rows fits a shared-memory stage", (long long)L);
     if (start != ISING_HOT && start != ISING_COLD) return fail(ISING_EINVAL, "bad start");
     if (sweeps < 1 || sweeps > kMaxSweeps) return fail(ISING_EINVAL, "sweeps out of range");
     if (tile_rows == 0 || !tile_rows_ok(L, tile_rows)) tile_rows = default_tile_rows(L);
@@ -1284,7 +1299,7 @@ int ising_batch_free(ising_batch_t b)
 int ising_autotune(int64_t L, int32_t* tile_rows, int32_t* threads, double* ms)
 {
     if (!tile_rows || !threads) return fail(ISING_EINVAL, "null output");
-    if (L < 64 || L % 64 || L > kPackedMaxL) return fail(ISING_EINVAL, "L must be a multiple of 64");
+    if (!packed_L_ok(L)) return fail(ISING_EINVAL, "L must be a multiple of 64 that a tile can hold");
     // time as many copies of the lattice as it takes to give every SM work (up to
     // 2^26 sites or 64 copies), as in a batch where this size is common
     int copies = 1;

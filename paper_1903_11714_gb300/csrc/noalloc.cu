@@ -145,6 +145,8 @@ extern "C" int ising_sweep_packed_noalloc(int32_t count, uint32_t* const* black,
         uint64_t T[2];
         if (ising_thresholds(beta[k], T) != ISING_OK) return set_error(ISING_EINVAL, "beta must be finite and >= 0");
         const int tr = tile_rows_for(L[k]);
+        if (stage_bytes(L[k], tr) > kNoAllocStageCap)
+            return set_error(ISING_EINVAL, "L too large for a shared-memory tile: L <= 163840 (L % 256 == 0) or L <= 102336");
         LatticeDesc& d = p.desc[k];
         d.plane[0] = black[k];
         d.plane[1] = white[k];

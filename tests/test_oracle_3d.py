@@ -244,3 +244,30 @@ def test_resume_equals_uninterrupted3d():
     c, Mc, Ec, _ = oracle.run3d(dims, 0.25, seed=4, sweeps=5, sweep0=4, state=b)
     assert np.array_equal(a, c)
     assert np.array_equal(Ma, np.concatenate([Mb, Mc])) and np.array_equal(Ea, np.concatenate([Eb, Ec]))
+
+
+# ------------------------------------------------ light-cone windows (3D)
+@pytest.mark.parametrize("origin,shape", [((0, 0, 0), (3, 4, 5)), ((14, 15, 13), (4, 3, 6)),
+                                          ((5, 9, 2), (2, 2, 2)), ((15, 17, 19), (1, 1, 1))])
+def test_window3d_matches_full_run(origin, shape):
+    # unequal extents, so that a transposed axis or a wrong plane index shows
+    dims, sweeps, beta, seed = (16, 18, 20), 3, BETA_C3, 41
+    full, _, _, _ = oracle.run3d(dims, beta, seed, oracle.HOT, sweeps)
+    win = oracle.window3d(dims, beta, seed, oracle.HOT, sweeps, origin, shape)
+    idx = [[(o + a) % n for a in range(s)] for o, s, n in zip(origin, shape, dims)]
+    assert np.array_equal(win, full[np.ix_(*idx)])
+
+
+def test_window3d_larger_than_torus_and_offset_sweeps():
+    # margin 2 * 4 = 8 exceeds every extent: the box wraps the torus more than once
+    dims, beta, seed = (6, 8, 4), 0.3, 9
+    full, _, _, _ = oracle.run3d(dims, beta, seed, oracle.COLD, 4)
+    win = oracle.window3d(dims, beta, seed, oracle.COLD, 4, (5, 7, 3), (2, 3, 2))
+    idx = [[(o + a) % n for a in range(s)] for o, s, n in zip((5, 7, 3), (2, 3, 2), dims)]
+    assert np.array_equal(win, full[np.ix_(*idx)])
+    # sweeps numbered from sweep0 = 5 draw other uniforms: the same as resuming the
+    # full chain at sweep 5 from the start state
+    start = oracle.init3d(dims, seed, oracle.HOT)
+    ref, _, _, _ = oracle.run3d(dims, beta, seed, sweeps=2, sweep0=5, state=start)
+    win5 = oracle.window3d(dims, beta, seed, oracle.HOT, 2, (0, 0, 0), dims, sweep0=5)
+    assert np.array_equal(win5, ref)
