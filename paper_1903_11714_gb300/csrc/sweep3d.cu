@@ -63,12 +63,15 @@ __device__ __forceinline__ void classify_word3d(uint32_t t, uint32_t up, uint32_
 
 // Words still undecided after the first two Philox calls wait in a per-warp queue;
 // an entry is two 16-byte slots: (position low, position high, undecided sites,
-// flips so far) and (h = 2 sites, h = 4 sites, old target word, unused).  Pushes
-// come 32 at most between drains of 32, so 64 entries suffice.
-constexpr int kQueueCap3 = 64;
+// flips so far) and (h = 2 sites, h = 4 sites, old target word, unused).  The
+// queue is checked (and drained 32 at a time while it holds 32) once per group of
+// four words, so it takes 31 + 4 * 32 entries (40 KB of static shared memory per
+// 256-thread CTA); checking once per group keeps the drain inlined at one place.
+constexpr int kQueueCap3 = 160;
 
 // Calls 2..7 for the top n queue entries, one per lane < n (every lane of the warp
-// takes part), then the words' final values and counts.
+// takes part), then the words' final values and, with COUNT, their counts.
+template <bool COUNT>
 __device__ __forceinline__ void drain_queue3d(const CubicDesc& d, uint32_t* tgt, const PhiloxWordConsts& pc_all,
                                               bool q_small, int colour, uint32_t sweep, uint4* wq, int& qn, int n,
                                               int lane, uint32_t& ups, uint32_t& anti)
@@ -92,7 +95,7 @@ __device__ __forceinline__ void drain_queue3d(const CubicDesc& d, uint32_t* tgt,
     if (act) {
         const uint32_t nw = e1.z ^ f[0];
         tgt[pos] = nw;
-        if (colour == 1) {
+        if (COUNT) {
             ups += __popc(nw);
             anti += 6u * __popc(f[0]) - 2u * __popc(f[0] & selB[0]) - 4u * __popc(f[0] & selA[0]);
         }
@@ -198,8 +201,10 @@ __device__ __forceinline__ void block_add_twice(unsigned long long a, unsigned l
 // Each word draws its first two Philox calls (8 bit planes) in step with its warp;
 // words with sites left wait in the warp's queue and are finished 32 at a time,
 // one per lane (the 2D tile routine does the same).  A queued word is stored twice:
-// as far as decided, then final (ordered by __syncwarp).
-template <int NT, int G>
+// as far as decided, then final (ordered by __syncwarp).  COUNT (the colour-1 pass)
+// adds the fused observables; as a template parameter it leaves the colour-0 pass
+// without their instructions.
+template <int NT, int G, bool COUNT>
 __global__ void __launch_bounds__(NT, 2) cubic_half_sweep_kernel(const __grid_constant__ CubicDesc d, int colour,
                                                                  uint32_t sweep)
 {
@@ -284,7 +289,7 @@ __global__ void __launch_bounds__(NT, 2) cubic_half_sweep_kernel(const __grid_co
             classify_word3d(t[k], n.up[k], n.dn[k], n.no[k], n.so[k], n.sm[k], n.hz[k], d, zero2, zero4, zero6, f[k],
                             und[k], selA[k], selB[k], anti0);
             if (!valid) und[k] = 0u;
-            if (colour == 1 && valid) {
+            if (COUNT && valid) {
                 ups += __popc(n.sm[k]);
                 anti += anti0;
             }
@@ -305,7 +310,7 @@ __global__ void __launch_bounds__(NT, 2) cubic_half_sweep_kernel(const __grid_co
 #pragma unroll
         for (int k = 0; k < G; ++k) {
             const bool pend = und[k] != 0u;
-            if (colour == 1 && valid && !pend) {
+            if (COUNT && valid && !pend) {
                 ups += __popc(nw[k]);
                 anti += 6u * __popc(f[k]) - 2u * __popc(f[k] & selB[k]) - 4u * __popc(f[k] & selA[k]);
             }
@@ -317,10 +322,12 @@ __global__ void __launch_bounds__(NT, 2) cubic_half_sweep_kernel(const __grid_co
                 wq[2 * slot + 1] = make_uint4(selA[k], selB[k], t[k], 0u);
             }
             qn += __popc(bal);
-            if (qn >= 32) {
-                __syncwarp();  // pushes visible to the draining lanes
-                drain_queue3d(d, tgt, pc_all, q_small, colour, sweep, wq, qn, 32, lane, ups, anti);
-            }
+        }
+        if (qn >= 32) {
+            __syncwarp();  // pushes visible to the draining lanes
+            do {
+                drain_queue3d<COUNT>(d, tgt, pc_all, q_small, colour, sweep, wq, qn, 32, lane, ups, anti);
+            } while (qn >= 32);
         }
         wg += step_w;
         j += step_j;
@@ -338,12 +345,12 @@ __global__ void __launch_bounds__(NT, 2) cubic_half_sweep_kernel(const __grid_co
     }
     if (qn > 0) {
         __syncwarp();
-        drain_queue3d(d, tgt, pc_all, q_small, colour, sweep, wq, qn, qn, lane, ups, anti);
+        drain_queue3d<COUNT>(d, tgt, pc_all, q_small, colour, sweep, wq, qn, qn, lane, ups, anti);
     }
     // a lane's bond count may be negative (a word's negative part can be added by
     // the lane that queued it and the rest by the lane that drained it), so it is
     // widened as a signed value; the block's total is not negative
-    if (colour == 1)
+    if (COUNT)
         block_add_twice<NT>(ups, (unsigned long long)(long long)(int32_t)anti, red, d.hist + 2 * (int64_t)sweep);
 }
 
@@ -452,10 +459,14 @@ cudaError_t launch_cubic_half_sweep(const CubicDesc& d, int colour, uint32_t swe
     const int64_t resident = 2 * (int64_t)sm_count();
     const int64_t need = (groups + kThreads3 - 1) / kThreads3;
     const int grid = (int)(need < resident ? need : resident);
-    if (G == 4)
-        cubic_half_sweep_kernel<kThreads3, 4><<<grid, kThreads3, 0, s>>>(d, colour, sweep);
+    if (G == 4 && colour == 1)
+        cubic_half_sweep_kernel<kThreads3, 4, true><<<grid, kThreads3, 0, s>>>(d, colour, sweep);
+    else if (G == 4)
+        cubic_half_sweep_kernel<kThreads3, 4, false><<<grid, kThreads3, 0, s>>>(d, colour, sweep);
+    else if (colour == 1)
+        cubic_half_sweep_kernel<kThreads3, 1, true><<<grid, kThreads3, 0, s>>>(d, colour, sweep);
     else
-        cubic_half_sweep_kernel<kThreads3, 1><<<grid, kThreads3, 0, s>>>(d, colour, sweep);
+        cubic_half_sweep_kernel<kThreads3, 1, false><<<grid, kThreads3, 0, s>>>(d, colour, sweep);
     return cudaGetLastError();
 }
 

@@ -215,8 +215,11 @@ __device__ __forceinline__ void store_group(uint32_t* p, const uint32_t v[G])
 
 // Entries of the per-warp queue of words still undecided after the first two
 // Philox calls: (word position in the tile, undecided sites, flips so far, h = 2
-// sites).  Pushes come 32 at most between drains of 32, so 64 entries suffice.
-constexpr int kQueueCap = 64;
+// sites).  The queue is checked (and drained 32 at a time while it holds 32) once
+// per group of words in CTAs of up to 256 threads, so it must take 31 + 4 * 32
+// entries; 512-thread CTAs check it after every two words and take 31 + 2 * 32, so
+// that two 100 KB tile stages and the queues still fit one CTA's shared memory.
+__host__ __device__ constexpr int queue_cap(int threads) { return threads <= 256 ? 160 : 96; }
 
 // Per-tile constants of the word update.
 struct TileCtx {
@@ -237,7 +240,8 @@ __device__ __forceinline__ PhiloxWordConsts group_consts(const TileCtx& x, const
 }
 
 // Calls 2..7 for the top n queue entries, one per lane < n (every lane of the warp
-// takes part), then the words' final values and counts.
+// takes part), then the words' final values and, with COUNT, their counts.
+template <bool COUNT>
 __device__ __forceinline__ void drain_queue(const TileCtx& x, const PhiloxWordConsts& pc_tile, uint4* wq, int& qn,
                                             int n, int lane, uint32_t& ups, uint32_t& anti)
 {
@@ -255,7 +259,7 @@ __device__ __forceinline__ void drain_queue(const TileCtx& x, const PhiloxWordCo
     if (act) {
         const uint32_t nw = x.s_tgt[e.x] ^ fm[0];
         x.out[e.x] = nw;
-        if (x.colour == 1) {
+        if (COUNT) {
             ups += __popc(nw);
             anti += 4u * __popc(fm[0]) - 2u * __popc(fm[0] & sel[0]);
         }
@@ -270,8 +274,10 @@ __device__ __forceinline__ void drain_queue(const TileCtx& x, const PhiloxWordCo
 // word per lane.  So the rare long comparisons no longer hold a whole warp, which
 // draws about 2.2 calls per word instead of the ~3.4 a warp-wide early exit needs.
 // A queued word is stored twice: as far as decided, then final (ordered by
-// __syncwarp).  Counts as in flip_masks.
-template <int NT, int G>
+// __syncwarp).  With COUNT (the colour-1 pass) the counts of flip_masks are added;
+// it is a template parameter so that the colour-0 pass carries none of their
+// instructions (predicated, they cost ~9 % of its issue slots).
+template <int NT, int G, bool COUNT>
 __device__ __forceinline__ void update_tile(const TileCtx& x, const PhiloxWordConsts& pc_tile, int nwords, uint4* wq,
                                             uint32_t& ups, uint32_t& anti)
 {
@@ -310,7 +316,7 @@ __device__ __forceinline__ void update_tile(const TileCtx& x, const PhiloxWordCo
             classify_word(tg[k], up[k], dn[k], sm[k], hz[k], x.all2, x.all4, x.zero2, x.zero4, fm[k], und[k],
                           sel[k], anti0);
             if (!valid) und[k] = 0u;
-            if (x.colour == 1 && valid) {
+            if (COUNT && valid) {
                 ups += __popc(sm[k]);
                 anti += anti0;
             }
@@ -334,16 +340,23 @@ __device__ __forceinline__ void update_tile(const TileCtx& x, const PhiloxWordCo
 #pragma unroll
         for (int k = 0; k < G; ++k) {
             const bool pend = und[k] != 0u;
-            if (x.colour == 1 && valid && !pend) {
+            if (COUNT && valid && !pend) {
                 ups += __popc(nw[k]);
                 anti += 4u * __popc(fm[k]) - 2u * __popc(fm[k] & sel[k]);
             }
             const uint32_t bal = __ballot_sync(0xffffffffu, pend);
             if (pend) wq[qn + __popc(bal & ((1u << lane) - 1u))] = make_uint4(pos0 + k, und[k], fm[k], sel[k]);
             qn += __popc(bal);
-            if (qn >= 32) {
-                __syncwarp();  // pushes visible to the draining lanes
-                drain_queue(x, pc_tile, wq, qn, 32, lane, ups, anti);
+            // the drain is inlined at few places: once per group (or per two words in
+            // 512-thread CTAs, whose queues are shorter)
+            constexpr int kEvery = (queue_cap(NT) - 31) / 32;
+            if ((k + 1) % kEvery == 0 || k == G - 1) {
+                if (qn >= 32) {
+                    __syncwarp();  // pushes visible to the draining lanes
+                    do {
+                        drain_queue<COUNT>(x, pc_tile, wq, qn, 32, lane, ups, anti);
+                    } while (qn >= 32);
+                }
             }
         }
         r += step_r;
@@ -355,7 +368,7 @@ __device__ __forceinline__ void update_tile(const TileCtx& x, const PhiloxWordCo
     }
     if (qn > 0) {
         __syncwarp();
-        drain_queue(x, pc_tile, wq, qn, qn, lane, ups, anti);
+        drain_queue<COUNT>(x, pc_tile, wq, qn, qn, lane, ups, anti);
     }
 }
 
@@ -374,7 +387,7 @@ __global__ void __launch_bounds__(NT, (ONE ? (ISING_SWEEP_THREADS_PER_SM / NT > 
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);
     uint32_t* red = reinterpret_cast<uint32_t*>(smem_raw + 16);  // 2 * NT/32 words
     uint4* queues = reinterpret_cast<uint4*>(smem_raw + 128 + ((2 * (NT / 32) * 4 + 127) / 128) * 128);
-    uint32_t* stages = reinterpret_cast<uint32_t*>(queues + (NT / 32) * kQueueCap);
+    uint32_t* stages = reinterpret_cast<uint32_t*>(queues + (NT / 32) * queue_cap(NT));
     const int tid = threadIdx.x;
     const int count = ONE ? 1 : *tt.count;
     const int total = ONE ? one.L / one.tile_rows : __ldg(tt.tile_start + count);
@@ -491,14 +504,23 @@ __global__ void __launch_bounds__(NT, (ONE ? (ISING_SWEEP_THREADS_PER_SM / NT > 
             x.par0 = (i0 + colour) & 1;
             x.q_small = L <= 131072;
             const PhiloxWordConsts pc_tile = philox_consts(key, 0u, sweep, (uint32_t)colour);
-            uint4* wq = queues + (tid >> 5) * kQueueCap;
+            uint4* wq = queues + (tid >> 5) * queue_cap(NT);
             const int nwords = TR * W;
-            if ((W & 3) == 0)
-                update_tile<NT, 4>(x, pc_tile, nwords, wq, ups, anti);
-            else if ((W & 1) == 0)
-                update_tile<NT, 2>(x, pc_tile, nwords, wq, ups, anti);
-            else
-                update_tile<NT, 1>(x, pc_tile, nwords, wq, ups, anti);
+            if (colour == 1) {
+                if ((W & 3) == 0)
+                    update_tile<NT, 4, true>(x, pc_tile, nwords, wq, ups, anti);
+                else if ((W & 1) == 0)
+                    update_tile<NT, 2, true>(x, pc_tile, nwords, wq, ups, anti);
+                else
+                    update_tile<NT, 1, true>(x, pc_tile, nwords, wq, ups, anti);
+            } else {
+                if ((W & 3) == 0)
+                    update_tile<NT, 4, false>(x, pc_tile, nwords, wq, ups, anti);
+                else if ((W & 1) == 0)
+                    update_tile<NT, 2, false>(x, pc_tile, nwords, wq, ups, anti);
+                else
+                    update_tile<NT, 1, false>(x, pc_tile, nwords, wq, ups, anti);
+            }
         }
         __syncthreads();
         buf ^= 1;
@@ -523,7 +545,7 @@ __global__ void packed_advance_kernel(LatticeDesc* desc, const int32_t* count, i
 
 int packed_smem_header_bytes(int threads)
 {
-    return 128 + ((2 * (threads / 32) * 4 + 127) / 128) * 128 + (threads / 32) * kQueueCap * 16;
+    return 128 + ((2 * (threads / 32) * 4 + 127) / 128) * 128 + (threads / 32) * queue_cap(threads) * 16;
 }
 
 template <int NT>
