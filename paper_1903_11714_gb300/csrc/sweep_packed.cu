@@ -20,10 +20,13 @@
 // after them finish from a per-warp queue (update_tile).
 //
 // Each persistent CTA walks the tile table: a tile is `tile_rows` full rows of
-// one lattice.  Thread 0 stages the tile's source rows (plus the halo rows above
-// and below, wrapped) and target rows into shared memory with bulk async copies
+// one lattice.  A tile's source rows (plus the halo rows above and below, wrapped)
+// and target rows are staged into shared memory with bulk async copies
 // (cp.async.bulk, completion on an mbarrier), double-buffered so the next tile
-// lands while the current one is computed.
+// lands while the current one is computed.  There is no CTA-wide barrier per tile:
+// each warp counts itself out of a stage when it is done with it, and the last warp
+// out issues the copies of the stage's next tile, so warps run up to a tile apart
+// instead of waiting for the slowest at every tile.
 #include "ising_internal.cuh"
 #include "philox.cuh"
 #include "word_update.cuh"
@@ -384,71 +387,87 @@ __global__ void __launch_bounds__(NT, (ONE ? (ISING_SWEEP_THREADS_PER_SM / NT > 
                              int* status, int stage_words_max, long long wait_limit, uint32_t extra_tx)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
+    // bars[0..1]: stage b filled (one arrival plus the copies' bytes); rel[b]: warps
+    // done with the tile in stage b (the last one refills it); acc, done: the
+    // single-lattice instance's block sums of the counts
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);
-    uint32_t* red = reinterpret_cast<uint32_t*>(smem_raw + 16);  // 2 * NT/32 words
+    uint32_t* rel = reinterpret_cast<uint32_t*>(smem_raw + 16);
+    uint32_t* done = reinterpret_cast<uint32_t*>(smem_raw + 24);
+    unsigned long long* acc = reinterpret_cast<unsigned long long*>(smem_raw + 32);
     uint4* queues = reinterpret_cast<uint4*>(smem_raw + 128 + ((2 * (NT / 32) * 4 + 127) / 128) * 128);
     uint32_t* stages = reinterpret_cast<uint32_t*>(queues + (NT / 32) * queue_cap(NT));
     const int tid = threadIdx.x;
     const int count = ONE ? 1 : *tt.count;
     const int total = ONE ? one.L / one.tile_rows : __ldg(tt.tile_start + count);
 
+    // Stage b serves this CTA's tiles tn, tn + 2g, tn + 4g, ... (g = gridDim.x): fill it
+    // with the first of them whose lattice is live (tiles of other lattices are skipped:
+    // their iterations neither wait for the stage nor release it).
+    auto fill = [&](int tn, int b) {
+        for (; tn < total; tn += 2 * gridDim.x) {
+            const TileInfo ti = tile_info<ONE>(tt, one, count, tn, step);
+            if (!ti.live) continue;
+            fence_proxy_async_smem();
+            issue_tile(desc_at<ONE>(tt, one, ti.lat), tn - tile_base<ONE>(tt, ti.lat), colour,
+                       stages + (size_t)b * stage_words_max, &bars[b], extra_tx);
+            return;
+        }
+    };
+
     if (tid == 0) {
         mbar_init(&bars[0], 1);
         mbar_init(&bars[1], 1);
+        rel[0] = 0;
+        rel[1] = 0;
+        *done = 0;
+        acc[0] = 0;
+        acc[1] = 0;
         fence_mbarrier_init();
     }
-    __syncthreads();
+    __syncthreads();  // the only CTA-wide barrier: from here on warps may run a tile apart
+    if (tid == 0) {
+        fill(blockIdx.x, 0);
+        fill(blockIdx.x + gridDim.x, 1);
+    }
 
     int buf = 0;
     uint32_t phase0 = 0, phase1 = 0;
     int t = blockIdx.x;
-    TileInfo cur = {0, false};
-    if (t < total) {
-        cur = tile_info<ONE>(tt, one, count, t, step);
-        if (cur.live && tid == 0)
-            issue_tile(desc_at<ONE>(tt, one, cur.lat), t - tile_base<ONE>(tt, cur.lat), colour, stages, &bars[0],
-                       extra_tx);
-    }
 
     int acc_lat = -1;          // lattice whose M/E counts are being accumulated
     uint32_t ups = 0, anti = 0;  // per-thread counts (colour-1 pass only)
 
-    auto flush = [&](int lat) {
-        // block reduction of (ups, anti) then one pair of 64-bit atomics
+    // warp reduction of (ups, anti); the warp's totals are counts of its own words, so
+    // their 32-bit sums are exact.  The multi-lattice instance adds them to the lattice's
+    // (M, E) slot per warp (warps reach a lattice change at different times); `last`
+    // (the single-lattice instance after its last tile) sums the CTA's warps in shared
+    // memory first, and the last warp to arrive adds the CTA's totals.
+    auto flush = [&](int lat, bool last) {
         const uint32_t u = __reduce_add_sync(0xffffffffu, ups);
         const uint32_t a = __reduce_add_sync(0xffffffffu, anti);
         if ((tid & 31) == 0) {
-            red[2 * (tid >> 5)] = u;
-            red[2 * (tid >> 5) + 1] = a;
-        }
-        __syncthreads();
-        if (tid == 0) {
-            unsigned long long su = 0, sa = 0;
-            for (int k = 0; k < NT / 32; ++k) {
-                su += red[2 * k];
-                sa += red[2 * k + 1];
-            }
             const LatticeDesc& d = desc_at<ONE>(tt, one, lat);
             int64_t* slot = d.hist + 2 * (int64_t)(d.sweep + (uint32_t)step);
-            atomicAdd(reinterpret_cast<unsigned long long*>(slot), 2ull * su);
-            atomicAdd(reinterpret_cast<unsigned long long*>(slot + 1), 2ull * sa);
+            if (last) {
+                atomicAdd(&acc[0], (unsigned long long)u);
+                atomicAdd(&acc[1], (unsigned long long)a);
+                __threadfence_block();
+                if (atomicAdd(done, 1u) == NT / 32 - 1) {
+                    __threadfence_block();
+                    atomicAdd(reinterpret_cast<unsigned long long*>(slot), 2ull * atomicAdd(&acc[0], 0ull));
+                    atomicAdd(reinterpret_cast<unsigned long long*>(slot + 1), 2ull * atomicAdd(&acc[1], 0ull));
+                }
+            } else {
+                atomicAdd(reinterpret_cast<unsigned long long*>(slot), 2ull * u);
+                atomicAdd(reinterpret_cast<unsigned long long*>(slot + 1), 2ull * a);
+            }
         }
-        __syncthreads();
         ups = 0;
         anti = 0;
     };
 
     for (; t < total; t += gridDim.x) {
-        const int tn = t + gridDim.x;
-        TileInfo nxt = {0, false};
-        if (tn < total) {
-            nxt = tile_info<ONE>(tt, one, count, tn, step);
-            if (nxt.live && tid == 0) {
-                fence_proxy_async_smem();
-                issue_tile(desc_at<ONE>(tt, one, nxt.lat), tn - tile_base<ONE>(tt, nxt.lat), colour,
-                           stages + (size_t)(buf ^ 1) * stage_words_max, &bars[buf ^ 1], extra_tx);
-            }
-        }
+        const TileInfo cur = tile_info<ONE>(tt, one, count, t, step);
         if (cur.live) {
             const LatticeDesc& d = desc_at<ONE>(tt, one, cur.lat);
             const int local_tile = t - tile_base<ONE>(tt, cur.lat);
@@ -458,14 +477,14 @@ __global__ void __launch_bounds__(NT, (ONE ? (ISING_SWEEP_THREADS_PER_SM / NT > 
                 phase1 ^= 1;
             else
                 phase0 ^= 1;
-            if (!__syncthreads_and(ok)) {
-                if (tid == 0) atomicExch(status, kStatusTimeout);
-                // give copies still in flight a bounded chance to land before exiting
-                if (nxt.live) mbar_wait_bounded(&bars[buf ^ 1], buf ? phase0 : phase1, wait_limit);
+            // the warp decides together (a lane that left alone would break the warp's votes);
+            // every wait of the CTA is bounded, so the other warps leave too
+            if (!__all_sync(0xffffffffu, ok)) {
+                atomicExch(status, kStatusTimeout);
                 return;
             }
             if (colour == 1 && acc_lat != cur.lat) {
-                if (acc_lat >= 0) flush(acc_lat);
+                if (acc_lat >= 0) flush(acc_lat, false);
                 acc_lat = cur.lat;
             }
             const int W = d.W, L = d.L, TR = d.tile_rows, HB = d.halo_rows;
@@ -521,12 +540,20 @@ __global__ void __launch_bounds__(NT, (ONE ? (ISING_SWEEP_THREADS_PER_SM / NT > 
                 else
                     update_tile<NT, 1, false>(x, pc_tile, nwords, wq, ups, anti);
             }
+            // this warp is done with the stage; the last warp to be done refills it
+            __syncwarp();
+            if ((tid & 31) == 0) {
+                __threadfence_block();
+                if (atomicAdd(&rel[buf], 1u) == NT / 32 - 1) {
+                    rel[buf] = 0;
+                    __threadfence_block();
+                    fill(t + 2 * gridDim.x, buf);
+                }
+            }
         }
-        __syncthreads();
         buf ^= 1;
-        cur = nxt;
     }
-    if (colour == 1 && acc_lat >= 0) flush(acc_lat);
+    if (colour == 1 && acc_lat >= 0) flush(acc_lat, ONE);
 }
 
 // After `steps` sweeps: advance each live lattice's sweep counter (bounded by its target).
