@@ -299,10 +299,14 @@ def run_batched(args, which: str) -> None:
     warm = graph * 3 if graph else args.warmup
     arena = sum(l.L * l.L // 8 + 16 * (l.sweeps + warm) + 4096 for l in lats)
     st = torch.cuda.Stream()
-    tiles = {}
+    # tile rows and CTA size from the autotuner; one CTA size serves the whole batch,
+    # that of the side carrying the most flips
+    tiles, tuned_threads = {}, {}
     for L in sorted({l.L for l in lats}):
-        tiles[L] = ising.ising_autotune(L)[0]
-    b = ising.Batch(len(lats), max_L, arena, 0, stream=st)
+        tiles[L], tuned_threads[L], _ = ising.ising_autotune(L)
+    work = {L: sum(l.L * l.L for l in lats if l.L == L) for L in tiles}
+    threads = tuned_threads[max(work, key=work.get)]
+    b = ising.Batch(len(lats), max_L, arena, threads, stream=st)
     for l in lats:
         b.add(l.L, l.beta, l.seed, l.start, l.sweeps + warm, tiles.get(l.L, 0))
     b.run(warm, graph_sweeps=graph)
@@ -338,7 +342,7 @@ def run_batched(args, which: str) -> None:
                       "unit": UNIT, "value": batched, "plain_int8_value": plain["int8"],
                       "plain_packed_value": plain["packed"], "lattices": len(lats), "sweeps": sweeps,
                       "graph_sweeps": graph, "ms": ms,
-                      "tile_rows_by_L": tiles or None,
+                      "tile_rows_by_L": tiles or None, "threads": threads,
                       "note": f"plain = each lattice alone with its own launches, {n_plain} sweeps each"}))
 
 
@@ -497,11 +501,14 @@ def run_serve(args) -> None:
     """Poisson arrivals at ~80 % of measured capacity; p50/p99 latency."""
     import torch
 
-    from paper_1903_11714_gb300 import serve, workloads
+    from paper_1903_11714_gb300 import ising, serve, workloads
 
     budget = int(args.serve_budget_gb * (1 << 30))
     st = torch.cuda.Stream()
-    srv = serve.Server(budget, slots=args.serve_slots, max_L=8192, quantum=args.serve_quantum, stream=st)
+    # CTA size from the autotuner at the largest request side, which carries most flips
+    threads = ising.ising_autotune(8192)[1]
+    srv = serve.Server(budget, slots=args.serve_slots, max_L=8192, quantum=args.serve_quantum, threads=threads,
+                       stream=st)
     # capacity: a saturated sample of the same request distribution, all present at t = 0
     calib = [workloads.Request(rid=r.rid, arrival=0.0, L=r.L, beta=r.beta, seed=r.seed, sweeps=r.sweeps)
              for r in workloads.serving_requests(args.serve_calib, 1.0, seed=55)]
@@ -518,7 +525,7 @@ def run_serve(args) -> None:
                       "p50_s": summ["p50_s"], "p99_s": summ["p99_s"], "requests": summ["completed"],
                       "rate_per_s": rate, "capacity_flips_per_ns": capacity / 1e9,
                       "mean_request_flips": mean_flips, "hbm_budget_gb": args.serve_budget_gb,
-                      "slots": args.serve_slots, "quantum_sweeps": args.serve_quantum,
+                      "slots": args.serve_slots, "quantum_sweeps": args.serve_quantum, "threads": threads,
                       "max_active": summ["max_active"], "max_arena_gb": summ["max_arena_bytes"] / 2**30,
                       "blocked_by_memory": summ["blocked_by_memory"], "blocked_by_slots": summ["blocked_by_slots"]}))
 
