@@ -84,6 +84,7 @@ def observables_from_planes(black, white, L, chunk=4096):
 
 @pytest.mark.parametrize("L,check_me", [
     (185_600, True),    # W = 2900: four-word groups, 2-row tiles
+    (272_896, True),    # the largest side (9.3 GB of planes): q's high word reaches 2
 ])
 def test_2d_past_32_bit_call_index(L, check_me):
     seed, sweeps = 7, 2
@@ -99,6 +100,9 @@ def test_2d_past_32_bit_call_index(L, check_me):
     rng = np.random.default_rng(L)
     spots = [(0, 0), (L - 3, L - 40), (r - 2, jb - 24), (r, L - 30), (L - 4, jb - 8)] + [
         (int(rng.integers(0, L)), int(rng.integers(0, L))) for _ in range(2)]
+    g2 = (2 << 32) // 8                      # first plane word with q's high word 2
+    if g2 < L * W:
+        spots.append((g2 // W - 1, 64 * (g2 % W) - 24))
     h, w_ = 6, 48
     for i0, j0 in spots:
         win = oracle.window(L, BC, seed, oracle.HOT, sweeps, i0, j0, h, w_)
@@ -107,6 +111,27 @@ def test_2d_past_32_bit_call_index(L, check_me):
     assert np.all(E % 4 == 0) and np.all(np.abs(E) <= 2 * L * L)
     if check_me:
         assert observables_from_planes(black, white, L) == (int(M[-1]), int(E[-1]))
+
+
+def test_2d_largest_width_not_a_multiple_of_four():
+    """L = 102,336 (W = 1599, odd): the largest side whose rows are not a whole number
+    of 16-byte units (4-row tiles with 4-row halos fill the 100 KB stage to within 64
+    bytes); windows at the seams and M/E of the last sweep."""
+    L, seed, sweeps = 102_336, 9, 2
+    W = L // 64
+    assert W % 2 == 1 and (4 + 8 + 4) * W * 4 <= 100 * 1024 < (4 + 8 + 4) * (W + 2) * 4
+    lat = ising.Lattice(L, BC, seed, ising.HOT, ising.PACKED)
+    lat.sweep(sweeps)
+    M, E = lat.history()
+    black, white = lat.get_planes()
+    lat.close()
+    rng = np.random.default_rng(L)
+    spots = [(0, 0), (L - 3, L - 40), (L // 2 + 1, 64 * (W - 1) + 40)] + [
+        (int(rng.integers(0, L)), int(rng.integers(0, L))) for _ in range(3)]
+    for i0, j0 in spots:
+        win = oracle.window(L, BC, seed, oracle.HOT, sweeps, i0, j0, 6, 48)
+        assert np.array_equal(window_from_planes(black, white, L, i0, j0, 6, 48), win), (i0, j0)
+    assert observables_from_planes(black, white, L) == (int(M[-1]), int(E[-1]))
 
 
 # ------------------------------------------------------------------------ 3D
