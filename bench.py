@@ -160,31 +160,41 @@ def committed_counters(kernel: str):
     with open(p) as f:
         d = json.load(f)
     sites = d["sites_per_launch"]
+    alu = d.get("alu_warp_inst_per_launch")
     return {"current": d.get("kernel_source_hash") == kernel_source_hash(kernel),
             "inst_slots_per_site": 32.0 * d["warp_inst_per_launch"] / sites,
+            "alu_ops_per_site": None if alu is None else 32.0 * alu / sites,
             "dram_bytes_per_site": (d["dram_bytes_read_per_launch"] + d["dram_bytes_write_per_launch"]) / sites,
             "capture": d.get("command")}
 
 
 def issue_roofline(kernel: str, sites_per_launch: float, t_launch_s: float, sm_max: float, peaks: dict) -> dict:
-    """Roofline of one half-sweep launch against the SM's instruction-issue rate."""
+    """Roofline of one half-sweep launch.  The binding unit is the ALU pipe (16 lanes x 4
+    schedulers per SM; the busiest pipe in the committed ncu counters), so `achieved` is
+    the launch's ALU-pipe thread operations (ncu sm__inst_executed_pipe_alu.sum x 32,
+    committed with a hash of the kernel's sources) per second of CUDA-event time, against
+    64 lanes/clk/SM x SMs x the maximum SM clock.  The instruction-issue view (every
+    instruction takes one of 128 thread slots/clk/SM) and the HBM view ride along."""
     c = committed_counters(kernel)
-    peak = ISSUE_SLOTS_PER_CLK_SM * N_SMS * sm_max * 1e6 / 1e12
+    alu_peak = ALU_OPS_PER_CLK_SM * N_SMS * sm_max * 1e6 / 1e12
+    issue_peak = ISSUE_SLOTS_PER_CLK_SM * N_SMS * sm_max * 1e6 / 1e12
     hbm_bytes = BYTES_PER_SITE_SWEEP * sites_per_launch
-    out = {"bound": "alu", "achieved": None, "peak": peak, "unit": "Tinst/s", "frac": None, "traffic": None,
-           "peak_basis": f"instruction issue: 4 schedulers x 32 lanes = {ISSUE_SLOTS_PER_CLK_SM:.0f} thread-instruction "
-                         f"slots/clk/SM x {N_SMS} SMs x {sm_max:.0f} MHz",
+    out = {"bound": "alu", "achieved": None, "peak": alu_peak, "unit": "Tops/s", "frac": None, "traffic": None,
+           "peak_basis": f"ALU pipe: 4 schedulers x 16 lanes = {ALU_OPS_PER_CLK_SM:.0f} thread operations/clk/SM x "
+                         f"{N_SMS} SMs x {sm_max:.0f} MHz (the probe in this line measures the lanes per clock)",
            "hbm_achieved_gbs": hbm_bytes / t_launch_s / 1e9, "hbm_peak_gbs": peaks.get("hbm_gbs", 6800.0)}
     if c is not None:
-        inst = c["inst_slots_per_site"] * sites_per_launch
-        out["achieved"] = inst / t_launch_s / 1e12
-        out["frac"] = out["achieved"] / peak
-        out["inst_slots_per_site"] = c["inst_slots_per_site"]
         out["counters"] = "current" if c["current"] else "stale: kernel source changed after the capture"
         if c["current"]:
             out["traffic"] = c["dram_bytes_per_site"] * sites_per_launch
-        out["alu_view"] = {"peak_tops": ALU_OPS_PER_CLK_SM * N_SMS * sm_max * 1e6 / 1e12,
-                           "note": "ALU pipe (16 lanes x 4 schedulers); its busy share is in the profile summary"}
+        if c["alu_ops_per_site"] is not None:
+            out["achieved"] = c["alu_ops_per_site"] * sites_per_launch / t_launch_s / 1e12
+            out["frac"] = out["achieved"] / alu_peak
+            out["alu_ops_per_site"] = c["alu_ops_per_site"]
+        issue = c["inst_slots_per_site"] * sites_per_launch / t_launch_s / 1e12
+        out["issue_view"] = {"achieved": issue, "peak": issue_peak, "unit": "Tinst/s", "frac": issue / issue_peak,
+                             "inst_slots_per_site": c["inst_slots_per_site"],
+                             "basis": f"{ISSUE_SLOTS_PER_CLK_SM:.0f} thread-instruction slots/clk/SM (4 schedulers x 32)"}
     return out
 
 
