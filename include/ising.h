@@ -90,9 +90,10 @@ int ising_thresholds(double beta, uint64_t T[2]);
 int ising_init(ising_t *out, int64_t L, double beta, uint64_t seed);
 
 /*
- * start: ISING_HOT or ISING_COLD.  kernel: ISING_PACKED (L % 64 == 0, 64 <= L, and
- * a double-buffered row tile must fit one 100 KB shared-memory stage: L <= 272896
- * when L % 256 == 0, else L <= 102336) or ISING_INT8 (L % 8 == 0, 8 <= L <= 131072).  stream: a cudaStream_t
+ * start: ISING_HOT or ISING_COLD.  kernel: ISING_PACKED (L % 64 == 0, 64 <= L <=
+ * 1048576 when L % 256 == 0 -- rows longer than 4,264 words are swept in 2-row
+ * column blocks -- else L <= 102336, so that a double-buffered tile of whole rows
+ * fits one 100 KB shared-memory stage) or ISING_INT8 (L % 8 == 0, 8 <= L <= 131072).  stream: a cudaStream_t
  * on which all of this handle's work is enqueued (the caller keeps it alive
  * until ising_free); NULL makes the handle create and own a non-blocking stream.  Device memory: packed L*L/8
  * bytes, int8 L*L bytes, plus 16 bytes of history per sweep (grown on demand).
@@ -133,6 +134,14 @@ int ising_moments(ising_t h, int64_t burn_in, double out[6], uint64_t sums[11]);
 
 /* Copies the lattice into out[L*L] (row-major, +1 / -1).  Synchronises. */
 int ising_get_lattice(ising_t h, int8_t *out);
+
+/*
+ * Copies rows row0 .. row0+nrows-1 of the lattice into out[nrows*L] (row-major,
+ * +1 / -1; for a cube the rows are r = i*L + j, L sites each), so that a window of a
+ * lattice too large for host memory can be read.  Caller-owned out.  Synchronises.
+ * Errors: EINVAL (rows outside the lattice, null out), ECUDA, ETIMEOUT.
+ */
+int ising_get_rows(ising_t h, int64_t row0, int64_t nrows, int8_t *out);
 
 /*
  * Replaces the lattice by in[L*L] (row-major, each entry +1 or -1; other values
@@ -221,6 +230,19 @@ int ising_batch_create(ising_batch_t *out, int32_t capacity, int64_t max_L, int6
 int ising_batch_add(ising_batch_t b, int64_t L, double beta, uint64_t seed, int32_t start, int64_t sweeps,
                     int32_t tile_rows, int32_t *idx);
 
+/*
+ * As ising_batch_add with the tile's width as well: tile_words = L/64 (whole rows),
+ * 0 (built-in: whole rows when they fit a stage, else column blocks), or a column
+ * block of tile_words words of each of tile_rows rows (tile_words a multiple of 4
+ * dividing L/64, below it; L % 256 == 0; tile_rows a power of two from 2 to 256
+ * dividing L, 0 = 2), each source row staged with 4 halo words on either side.  The
+ * chain does not depend on the tile shape.  Errors as ising_batch_add, and EINVAL
+ * for a block that is not of that form or whose stage exceeds the batch's (the
+ * largest built-in stage of its sides).
+ */
+int ising_batch_add_tiled(ising_batch_t b, int64_t L, double beta, uint64_t seed, int32_t start, int64_t sweeps,
+                          int32_t tile_rows, int32_t tile_words, int32_t *idx);
+
 /* Frees a slot and its arena memory (after the stream's pending work). */
 int ising_batch_remove(ising_batch_t b, int32_t idx);
 
@@ -264,8 +286,10 @@ int ising_batch_free(ising_batch_t b);
  * Times sweeps of packed lattices of side L for each candidate (tile_rows a
  * power of two from 2 to 256 accepted by ising_batch_add; threads 256 or 512),
  * using enough copies of the lattice (up to 2^26 sites or 64) to give every SM
- * work, and returns the fastest in *tile_rows, *threads and its time per sweep of
- * one lattice in *ms.  Uses its own scratch batch.  Errors: EINVAL, ENOMEM, ECUDA.
+ * work, each candidate timed twice over about 2^32 site updates (16 to 256 sweeps),
+ * and returns the fastest in *tile_rows, *threads and its time per sweep of one
+ * lattice in *ms.  Whole-row tiles only: EINVAL for L whose rows need column blocks
+ * (L > 272896).  Uses its own scratch batch.  Errors: EINVAL, ENOMEM, ECUDA.
  */
 int ising_autotune(int64_t L, int32_t *tile_rows, int32_t *threads, double *ms);
 

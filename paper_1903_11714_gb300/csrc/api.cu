@@ -47,9 +47,10 @@ int cuda_fail(cudaError_t e, const char* what)
         if (e_ != cudaSuccess) return cuda_fail(e_, #call);    \
     } while (0)
 
-// Largest packed side: a double-buffered tile of 2 rows (plus 1-row halos) must fit
-// in one 100 KB stage, i.e. W = L/64 <= 4264 (see packed_L_ok for other W).
-constexpr int64_t kPackedMaxL = 272896;
+// Largest packed side (2^40 sites, 128 GB of planes).  Rows too long for a whole-row
+// tile (W = L/64 > 4264) are cut into column blocks, which needs W % 4 == 0 (see
+// packed_L_ok).
+constexpr int64_t kPackedMaxL = 1 << 20;
 constexpr int64_t kInt8MaxL = 1 << 17;
 constexpr uint32_t kNoTarget = 0xFFFFFFFFu;
 constexpr int64_t kMaxSweeps = 0xFFFFFFFEll;  // sweep counter is a 32-bit Philox counter word
@@ -83,10 +84,10 @@ void set_thresholds(LatticeDesc& d, const uint64_t T[2])
 
 int halo_rows_for(int64_t W) { return (W % 4 == 0) ? 1 : 4; }
 
-int64_t stage_bytes_for(int64_t L, int tile_rows)
+int64_t stage_bytes_for(int64_t L, int tile_rows, int tile_words = 0)
 {
     const int64_t W = L / 64;
-    const int64_t words = stage_words((int32_t)W, tile_rows, halo_rows_for(W));
+    const int64_t words = stage_words((int32_t)W, tile_rows, halo_rows_for(W), tile_words);
     return (words * 4 + 15) / 16 * 16;
 }
 
@@ -102,15 +103,49 @@ bool tile_rows_ok(int64_t L, int tr)
            stage_bytes_for(L, tr) <= kStageCapBytes;
 }
 
-// A packed side the tiled kernel can sweep: L % 64 == 0, 64 <= L, and some tile height
-// fits a stage -- L <= 272,896 when L % 256 == 0 (2-row tiles, 1-row halos), else
-// L <= 102,336 (4-row tiles with 4-row halos).
-bool packed_L_ok(int64_t L)
+// Column blocks: tile_words = cw < W words of each of tile_rows rows, staged with 4 halo
+// words on either side; cw a multiple of 4 dividing W (so W % 4 == 0 and halo rows are
+// single rows), below 2^16 (queue entries hold a word's place in 16 bits).
+bool tile_ok(int64_t L, int tr, int cw)
 {
-    if (L < 64 || L % 64 || L > kPackedMaxL) return false;
+    const int64_t W = L / 64;
+    if (cw == 0 || cw == W) return tile_rows_ok(L, tr);
+    const bool pow2 = tr >= 2 && tr <= kMaxTileRows && (tr & (tr - 1)) == 0;
+    return pow2 && W % 4 == 0 && cw >= 4 && cw % 4 == 0 && cw < W && W % cw == 0 && cw < 65536 && L % tr == 0 &&
+           stage_bytes_for(L, tr, cw) <= kStageCapBytes;
+}
+
+// Whole rows fit some tile height.
+bool whole_rows_ok(int64_t L)
+{
     for (int tr = 2; tr <= kMaxTileRows; tr <<= 1)
         if (tile_rows_ok(L, tr)) return true;
     return false;
+}
+
+// Column width of a lattice whose rows are too long for whole-row tiles: the largest
+// divisor of W that is a multiple of 4 and at most kBlockWords (2-row blocks of 1,024
+// words then take 25 KB per stage, so two CTAs fit an SM); W when whole rows fit; 0
+// when neither can be had (W % 4 != 0).
+constexpr int kBlockWords = 1024;
+int default_tile_words(int64_t L)
+{
+    const int64_t W = L / 64;
+    if (whole_rows_ok(L)) return (int)W;
+    if (W % 4) return 0;
+    for (int64_t cw = std::min<int64_t>(W - 4, kBlockWords) / 4 * 4; cw >= 4; cw -= 4)
+        if (W % cw == 0 && tile_ok(L, 2, (int)cw)) return (int)cw;
+    return 0;
+}
+
+// A packed side the tiled kernel can sweep: L % 64 == 0, 64 <= L <= 2^20, and a tile
+// of some shape fits a stage -- any such L when L % 256 == 0 (whole rows up to
+// L = 272,896, column blocks beyond), else L <= 102,336 (whole rows: 4-row tiles with
+// 4-row halos).
+bool packed_L_ok(int64_t L)
+{
+    if (L < 64 || L % 64 || L > kPackedMaxL) return false;
+    return default_tile_words(L) != 0;
 }
 
 // Built-in tile height: about ISING_TILE_WORDS words per tile and at most 64 rows.
@@ -162,6 +197,13 @@ struct Engine {
     const LatticeDesc* one = nullptr;
     bool capturing = false;
     bool one_lattice = false;  // launches the single-lattice instance (sizes the grid by its occupancy)
+    bool blocks = false;       // some lattice has column-block tiles (launch the build that handles them)
+
+    void allow_blocks()
+    {
+        if (!blocks) drop_graph();  // a captured graph holds the whole-row build
+        blocks = true;
+    }
 
     int setup(int max_count_, int stage_bytes_, int threads_, cudaStream_t s, bool one_lattice_ = false)
     {
@@ -232,7 +274,7 @@ struct Engine {
         for (int64_t k = 0; k < n; ++k) {
             for (int c = 0; c < 2; ++c) {
                 cudaError_t e = launch_packed_half_sweep(tt, c, (int)k, d_status, grid, threads, stage_bytes, stream,
-                                                         kWaitLimitCycles, 0u, by_value);
+                                                         kWaitLimitCycles, 0u, by_value, blocks);
                 if (e != cudaSuccess) return cuda_fail(e, "packed half-sweep launch");
             }
         }
@@ -472,15 +514,17 @@ CubicDesc cubic_desc(ising_t h)
 }
 
 // int8 copy of a cubic lattice, index (i*L + j)*L + k, through a bounded staging buffer.
-int cubic_to_host(ising_t h, int8_t* out)
+// Rows [row0, row0 + nrows) (row r = i*L + j, L sites each) of a cube into out.
+int cubic_rows_to_host(ising_t h, int64_t row0, int64_t nrows, int8_t* out)
 {
-    const int64_t L = h->L, rows = L * L;
-    const int64_t chunk = std::min<int64_t>(rows, std::max<int64_t>(1, (int64_t)(256ll << 20) / L));
+    const int64_t L = h->L;
+    const int64_t chunk = std::min<int64_t>(nrows, std::max<int64_t>(1, (int64_t)(256ll << 20) / L));
     int8_t* tmp = nullptr;
     CK(cudaMalloc(&tmp, (size_t)(chunk * L)));
-    for (int64_t r0 = 0; r0 < rows; r0 += chunk) {
-        const int64_t nr = std::min<int64_t>(chunk, rows - r0);
-        cudaError_t e = launch_cubic_unpack(h->planes, h->planes + plane_words(h), tmp, L, r0, nr, h->stream);
+    for (int64_t r0 = 0; r0 < nrows; r0 += chunk) {
+        const int64_t nr = std::min<int64_t>(chunk, nrows - r0);
+        cudaError_t e =
+            launch_cubic_unpack(h->planes, h->planes + plane_words(h), tmp, L, row0 + r0, nr, h->stream);
         if (e == cudaSuccess) e = cudaMemcpyAsync(out + r0 * L, tmp, (size_t)(nr * L), cudaMemcpyDeviceToHost, h->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
         if (e != cudaSuccess) {
@@ -492,6 +536,8 @@ int cubic_to_host(ising_t h, int8_t* out)
     return ISING_OK;
 }
 
+int cubic_to_host(ising_t h, int8_t* out) { return cubic_rows_to_host(h, 0, h->L * h->L, out); }
+
 int read_status(ising_t h)
 {
     if (h->kernel == ISING_PACKED) return h->eng.check_status();
@@ -500,15 +546,17 @@ int read_status(ising_t h)
 }
 
 // Copies the lattice to host int8 through a bounded device staging buffer.
-int packed_to_host(const uint32_t* black, const uint32_t* white, int64_t L, int8_t* out, cudaStream_t s)
+// Rows [row0, row0 + nrows) of a packed lattice as int8 spins into out (nrows * L bytes).
+int packed_rows_to_host(const uint32_t* black, const uint32_t* white, int64_t L, int64_t row0, int64_t nrows,
+                        int8_t* out, cudaStream_t s)
 {
     const int64_t rows_per = std::max<int64_t>(1, (int64_t)(256ll << 20) / L);
-    const int64_t chunk_rows = std::min<int64_t>(L, rows_per);
+    const int64_t chunk_rows = std::min<int64_t>(nrows, rows_per);
     int8_t* tmp = nullptr;
     CK(cudaMalloc(&tmp, (size_t)(chunk_rows * L)));
-    for (int64_t r0 = 0; r0 < L; r0 += chunk_rows) {
-        const int64_t nr = std::min<int64_t>(chunk_rows, L - r0);
-        cudaError_t e = launch_unpack(black, white, tmp, L, r0, nr, s);
+    for (int64_t r0 = 0; r0 < nrows; r0 += chunk_rows) {
+        const int64_t nr = std::min<int64_t>(chunk_rows, nrows - r0);
+        cudaError_t e = launch_unpack(black, white, tmp, L, row0 + r0, nr, s);
         if (e == cudaSuccess) e = cudaMemcpyAsync(out + r0 * L, tmp, (size_t)(nr * L), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) {
@@ -518,6 +566,11 @@ int packed_to_host(const uint32_t* black, const uint32_t* white, int64_t L, int8
     }
     cudaFree(tmp);
     return ISING_OK;
+}
+
+int packed_to_host(const uint32_t* black, const uint32_t* white, int64_t L, int8_t* out, cudaStream_t s)
+{
+    return packed_rows_to_host(black, white, L, 0, L, out, s);
 }
 
 int host_to_packed(const int8_t* in, uint32_t* black, uint32_t* white, int64_t L, cudaStream_t s)
@@ -638,7 +691,9 @@ int ising_init_ex(ising_t* out, int64_t L, double beta, uint64_t seed, int start
         const int64_t plane_words = L * (L / 64);
         CKH(cudaMalloc(&h->planes, sizeof(uint32_t) * 2 * (size_t)plane_words));
         CKH(launch_packed_init(h->planes, h->planes + plane_words, L, seed, start, h->stream));
-        const int tr = single_tile_rows(L);
+        // whole rows when they fit a tile, else 2-row column blocks
+        const int cw = default_tile_words(L);
+        const int tr = cw == (int)(L / 64) ? single_tile_rows(L) : 2;
         LatticeDesc& d = h->desc;
         d.plane[0] = h->planes;
         d.plane[1] = h->planes + plane_words;
@@ -649,16 +704,18 @@ int ising_init_ex(ising_t* out, int64_t L, double beta, uint64_t seed, int start
         set_thresholds(d, T);
         d.tile_rows = tr;
         d.halo_rows = halo_rows_for(L / 64);
+        d.tile_words = cw;
         d.sweep = 0;
         d.target = kNoTarget;
         d.active = 1;
-        rc = h->eng.setup(1, (int)stage_bytes_for(L, tr), 256, h->stream, true);
+        rc = h->eng.setup(1, (int)stage_bytes_for(L, tr, cw), 256, h->stream, true);
         if (rc) {
             destroy_handle(h);
             return rc;
         }
         h->eng.one = &h->desc;
-        std::vector<int32_t> ts = {0, (int32_t)(L / tr)};
+        if (cw != (int)(L / 64)) h->eng.allow_blocks();
+        std::vector<int32_t> ts = {0, (int32_t)lattice_tiles(L, tr, cw)};
         rc = h->eng.upload_tiles(ts, 1);
         if (!rc) rc = ensure_hist(h, 1024);
         if (rc) {
@@ -866,6 +923,26 @@ int ising_get_lattice(ising_t h, int8_t* out)
     return ISING_OK;
 }
 
+int ising_get_rows(ising_t h, int64_t row0, int64_t nrows, int8_t* out)
+{
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (!out && nrows > 0) return fail(ISING_EINVAL, "null output");
+    const int64_t L = h->L, rows = h->kernel == kKernelCubic ? L * L : L;
+    if (row0 < 0 || nrows < 0 || nrows > rows - row0)
+        return fail(ISING_EINVAL, "rows %lld .. %lld outside 0 .. %lld", (long long)row0, (long long)(row0 + nrows),
+                    (long long)rows);
+    if (nrows == 0) return ISING_OK;
+    rc = read_status(h);
+    if (rc) return rc;
+    if (h->kernel == kKernelCubic) return cubic_rows_to_host(h, row0, nrows, out);
+    if (h->kernel == ISING_PACKED)
+        return packed_rows_to_host(h->planes, h->planes + L * (L / 64), L, row0, nrows, out, h->stream);
+    CK(cudaMemcpyAsync(out, h->lat + row0 * L, (size_t)(nrows * L), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return ISING_OK;
+}
+
 int ising_set_lattice(ising_t h, const int8_t* in)
 {
     int rc = check_handle(h);
@@ -1029,7 +1106,7 @@ int rebuild_tiles(ising_batch_t b)
     std::vector<int32_t> ts((size_t)count + 1, 0);
     for (int k = 0; k < count; ++k) {
         const auto& s = b->slots[k];
-        ts[k + 1] = ts[k] + (s.used ? (int32_t)(s.L / s.desc.tile_rows) : 0);
+        ts[k + 1] = ts[k] + (s.used ? (int32_t)lattice_tiles(s.L, s.desc.tile_rows, s.desc.tile_words) : 0);
     }
     b->count = count;
     return b->eng.upload_tiles(ts, count);
@@ -1072,11 +1149,15 @@ int ising_batch_create(ising_batch_t* out, int32_t capacity, int64_t max_L, int6
         delete b;
         return rc;
     }
-    // stage size: the largest tile any admissible lattice can use
+    // stage size: the largest tile any admissible lattice can use by default (whole
+    // rows, or the built-in column blocks of rows too long for them); a column block
+    // asked for in ising_batch_add_tiled must fit this too
     int64_t stage = 0;
-    for (int64_t L = 64; L <= max_L; L += 64)
+    for (int64_t L = 64; L <= max_L; L += 64) {
         for (int tr = 2; tr <= kMaxTileRows; tr *= 2)
             if (tile_rows_ok(L, tr)) stage = std::max(stage, stage_bytes_for(L, tr));
+        if (L % 256 == 0 && !whole_rows_ok(L)) stage = std::max(stage, stage_bytes_for(L, 2, default_tile_words(L)));
+    }
     rc = b->eng.setup(capacity, (int)stage, threads, b->stream);
     if (!rc) rc = b->arena.init(arena_bytes);
     if (!rc) {
@@ -1097,6 +1178,12 @@ int ising_batch_create(ising_batch_t* out, int32_t capacity, int64_t max_L, int6
 int ising_batch_add(ising_batch_t b, int64_t L, double beta, uint64_t seed, int32_t start, int64_t sweeps,
                     int32_t tile_rows, int32_t* idx)
 {
+    return ising_batch_add_tiled(b, L, beta, seed, start, sweeps, tile_rows, 0, idx);
+}
+
+int ising_batch_add_tiled(ising_batch_t b, int64_t L, double beta, uint64_t seed, int32_t start, int64_t sweeps,
+                          int32_t tile_rows, int32_t tile_words, int32_t* idx)
+{
     if (!b || !idx) return fail(ISING_EINVAL, "null argument");
     uint64_t T[2];
     if (!thresholds(beta, T)) return fail(ISING_EINVAL, "beta must be finite and >= 0");
@@ -1104,7 +1191,18 @@ int ising_batch_add(ising_batch_t b, int64_t L, double beta, uint64_t seed, int3
     if (!packed_L_ok(L)) return fail(ISING_EINVAL, "no tile of L = %lld rows fits a shared-memory stage", (long long)L);
     if (start != ISING_HOT && start != ISING_COLD) return fail(ISING_EINVAL, "bad start");
     if (sweeps < 1 || sweeps > kMaxSweeps) return fail(ISING_EINVAL, "sweeps out of range");
-    if (tile_rows == 0 || !tile_rows_ok(L, tile_rows)) tile_rows = default_tile_rows(L);
+    const int W = (int)(L / 64);
+    if (tile_words == 0) tile_words = default_tile_words(L);
+    if (tile_words == W) {
+        if (tile_rows == 0 || !tile_rows_ok(L, tile_rows)) tile_rows = default_tile_rows(L);
+    } else {
+        if (tile_rows == 0) tile_rows = 2;
+        if (!tile_ok(L, tile_rows, tile_words))
+            return fail(ISING_EINVAL, "tile of %d rows x %d words is not a column block of L = %lld", tile_rows,
+                        tile_words, (long long)L);
+    }
+    if (stage_bytes_for(L, tile_rows, tile_words) > b->eng.stage_bytes)
+        return fail(ISING_EINVAL, "tile of %d rows x %d words exceeds the batch's stage", tile_rows, tile_words);
     int slot = -1;
     for (int k = 0; k < b->capacity; ++k)
         if (!b->slots[k].used) {
@@ -1137,8 +1235,10 @@ int ising_batch_add(ising_batch_t b, int64_t L, double beta, uint64_t seed, int3
     set_thresholds(d, T);
     d.tile_rows = tile_rows;
     d.halo_rows = halo_rows_for(L / 64);
+    d.tile_words = tile_words;
     d.sweep = 0;
     d.target = (uint32_t)sweeps;
+    if (tile_words != W) b->eng.allow_blocks();
     d.active = 1;
     cudaError_t e = launch_packed_init(d.plane[0], d.plane[1], L, seed, start, b->stream);
     if (e != cudaSuccess) return cuda_fail(e, "init launch");
@@ -1300,34 +1400,43 @@ int ising_autotune(int64_t L, int32_t* tile_rows, int32_t* threads, double* ms)
 {
     if (!tile_rows || !threads) return fail(ISING_EINVAL, "null output");
     if (!packed_L_ok(L)) return fail(ISING_EINVAL, "L must be a multiple of 64 that a tile can hold");
+    if (!whole_rows_ok(L)) return fail(ISING_EINVAL, "the autotuner times whole-row tiles (L <= 272896)");
     // time as many copies of the lattice as it takes to give every SM work (up to
     // 2^26 sites or 64 copies), as in a batch where this size is common
     int copies = 1;
     while (copies < 64 && (int64_t)copies * L * L < (1ll << 26)) copies *= 2;
-    const int reps = L >= 8192 ? 4 : 16;
+    // sweeps per timing: about 2^32 site updates (at least 16, at most 256), so that a
+    // candidate's time is long against launch jitter; each candidate is timed twice and
+    // its better time kept
+    const int64_t per_sweep_sites = (int64_t)copies * L * L;
+    const int reps = (int)std::min<int64_t>(256, std::max<int64_t>(16, (1ll << 32) / per_sweep_sites));
     double best = 1e300;
     int best_tr = 0, best_th = 0;
     const int thread_opts[2] = {256, 512};
     for (int ti = 0; ti < 2; ++ti) {
         ising_batch_t b = nullptr;
-        const int64_t per = (int64_t)sizeof(uint32_t) * 2 * L * (L / 64) + 16 * (reps + 4) + 512;
+        const int64_t per = (int64_t)sizeof(uint32_t) * 2 * L * (L / 64) + 16 * (2 * reps + 4) + 512;
         int rc = ising_batch_create(&b, copies, L, per * copies + 4096, thread_opts[ti], nullptr);
         if (rc) return rc;
         for (int tr = 2; tr <= kMaxTileRows; tr *= 2) {
-            if (!tile_rows_ok(L, tr)) continue;
+            if (!tile_rows_ok(L, tr)) continue;  // whole rows only
             std::vector<int32_t> idx((size_t)copies, -1);
             for (int k = 0; k < copies && !rc; ++k)
-                rc = ising_batch_add(b, L, 0.4406868, 12345 + k, ISING_HOT, reps + 4, tr, &idx[(size_t)k]);
+                rc = ising_batch_add(b, L, 0.4406868, 12345 + k, ISING_HOT, 2 * reps + 4, tr, &idx[(size_t)k]);
             cudaEvent_t e0, e1;
             cudaEventCreate(&e0);
             cudaEventCreate(&e1);
             if (!rc) rc = b->eng.run(2, 0);  // warm-up
-            cudaEventRecord(e0, b->stream);
-            if (!rc) rc = b->eng.run(reps, 0);
-            cudaEventRecord(e1, b->stream);
-            cudaEventSynchronize(e1);
-            float t = 0;
-            cudaEventElapsedTime(&t, e0, e1);
+            float t = 1e30f;
+            for (int m = 0; m < 2 && !rc; ++m) {
+                cudaEventRecord(e0, b->stream);
+                rc = b->eng.run(reps, 0);
+                cudaEventRecord(e1, b->stream);
+                cudaEventSynchronize(e1);
+                float tm = 0;
+                cudaEventElapsedTime(&tm, e0, e1);
+                t = std::min(t, tm);
+            }
             cudaEventDestroy(e0);
             cudaEventDestroy(e1);
             if (!rc) rc = b->eng.check_status();

@@ -25,7 +25,9 @@ struct LatticeDesc {
     uint32_t sweep;       // index of the next sweep of this lattice
     uint32_t target;      // sweeps stop at this index (serving); 0xFFFFFFFF otherwise
     int32_t active;       // 0: skipped by the kernels
-    int32_t pad_;
+    int32_t tile_words;   // words per tile row: W (whole rows), or a divisor of W that is a
+                          // multiple of 4 (W % 4 == 0): column blocks, each source row
+                          // staged with 4 halo words on either side
 };
 static_assert(sizeof(LatticeDesc) % 16 == 0, "descriptor alignment");
 
@@ -37,10 +39,22 @@ struct TileTable {
     const int32_t* count;       // device scalar: number of lattices
 };
 
-// Shared-memory bytes of one pipeline stage for a lattice's tile.
-__host__ __device__ inline int64_t stage_words(int32_t W, int32_t tile_rows, int32_t halo_rows)
+// Words of one pipeline stage for a lattice's tile: source rows (with halos) then
+// target rows.  Whole-row tiles (tile_words == W) stage rows of W words; column
+// blocks stage source rows of tile_words + 8 words (4 halo words on either side).
+__host__ __device__ inline int64_t stage_words(int32_t W, int32_t tile_rows, int32_t halo_rows,
+                                               int32_t tile_words = 0)
 {
-    return (int64_t)(tile_rows + 2 * halo_rows) * W + (int64_t)tile_rows * W;
+    if (tile_words == 0 || tile_words == W)
+        return (int64_t)(tile_rows + 2 * halo_rows) * W + (int64_t)tile_rows * W;
+    return (int64_t)(tile_rows + 2 * halo_rows) * (tile_words + 8) + (int64_t)tile_rows * tile_words;
+}
+
+// Tiles of one lattice: row blocks times column blocks.
+__host__ __device__ inline int64_t lattice_tiles(int64_t L, int32_t tile_rows, int32_t tile_words)
+{
+    const int64_t W = L / 64;
+    return (L / tile_rows) * (W / (tile_words ? tile_words : W));
 }
 
 // Bound on every mbarrier wait of the sweep kernel, in SM clocks (~2 s at 2 GHz,
@@ -52,11 +66,12 @@ constexpr long long kWaitLimitCycles = 4000000000LL;
 // barrier expect bytes that never arrive: only the timeout self-test uses it.
 // one != nullptr: a launch over that single lattice, whose descriptor (with the
 // sweep index the host knows) is passed by value; tt is then not read.  Not for
-// graph capture, since the sweep index is baked into the launch.
+// graph capture, since the sweep index is baked into the launch.  blocks: some
+// lattice of tt may have column-block tiles (tile_words < W).
 cudaError_t launch_packed_half_sweep(const TileTable& tt, int colour, int step, int* status, int grid,
                                      int threads, int smem_stage_bytes, cudaStream_t s,
                                      long long wait_limit = kWaitLimitCycles, uint32_t extra_tx = 0,
-                                     const LatticeDesc* one = nullptr);
+                                     const LatticeDesc* one = nullptr, bool blocks = false);
 // One small lattice (L <= packed_resident_max_L()) swept nsweeps times by a single
 // CTA holding both planes in shared memory; writes hist[d.sweep .. +nsweeps).
 int packed_resident_max_L();

@@ -161,6 +161,7 @@ extern "C" int ising_sweep_packed_noalloc(int32_t count, uint32_t* const* black,
         d.all4 = T[1] >= 4294967296ull ? 0xFFFFFFFFu : 0u;
         d.tile_rows = tr;
         d.halo_rows = (int32_t)halo_rows(L[k] / 64);
+        d.tile_words = (int32_t)(L[k] / 64);  // whole rows
         d.sweep = (uint32_t)first_sweep;
         d.target = 0xFFFFFFFFu;
         d.active = 1;

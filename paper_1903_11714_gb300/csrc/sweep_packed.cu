@@ -166,10 +166,49 @@ __device__ __forceinline__ int tile_base(const TileTable& tt, int lat)
 // W % 4 == 0 every row does (TR may then be 2); otherwise HB = 4 and tiles start
 // on rows that are multiples of 4, so each copied block starts at a multiple of
 // 4 rows.
+//
+// Column blocks (tile_words = CW < W, W % 4 == 0, HB = 1): tile (row block rb, column
+// block cb) covers rows i0 = rb * TR .. and words w0 = cb * CW .. w0 + CW - 1.  Each
+// source row is staged as words w0 - 4 .. w0 + CW + 3 (CW + 8 words; the 4 words on
+// either side, wrapped round the row at its ends, give the horizontal neighbours of
+// the block's edge words), each target row as its CW words.  All copies are whole
+// 16-byte units at 16-byte boundaries.
+//
+// TILES: 0 = whole rows only, 1 = column blocks only, 2 = either (decided per lattice).
+template <int TILES>
 __device__ __forceinline__ void issue_tile(const LatticeDesc& d, int local_tile, int colour, uint32_t* stage,
                                            uint64_t* bar, uint32_t extra_tx)
 {
-    const int W = d.W, L = d.L, TR = d.tile_rows, HB = d.halo_rows;
+    const int W = d.W, L = d.L, TR = d.tile_rows, HB = d.halo_rows, CW = d.tile_words ? d.tile_words : W;
+    if (TILES != 0 && (TILES == 1 || CW != W)) {
+        const int ncb = W / CW;
+        const int rb = local_tile / ncb, cb = local_tile - rb * ncb;
+        const int i0 = rb * TR, w0 = cb * CW, SW = CW + 8;
+        const uint32_t* src = d.plane[colour ^ 1];
+        const uint32_t* tgt = d.plane[colour];
+        uint32_t* s_src = stage;
+        uint32_t* s_tgt = stage + (size_t)(TR + 2 * HB) * SW;
+        mbar_expect_tx(bar, 4u * (uint32_t)((TR + 2 * HB) * SW + TR * CW) + extra_tx);
+        for (int a = 0; a < TR + 2 * HB; ++a) {
+            int row = i0 - HB + a;
+            if (row < 0) row += L;
+            if (row >= L) row -= L;
+            const uint32_t* rp = src + (size_t)row * W;
+            uint32_t* dst = s_src + (size_t)a * SW;
+            if (w0 == 0) {
+                bulk_copy_g2s(dst, rp + W - 4, 16u, bar);
+                bulk_copy_g2s(dst + 4, rp, 4u * (uint32_t)(CW + 4), bar);
+            } else if (w0 + CW == W) {
+                bulk_copy_g2s(dst, rp + w0 - 4, 4u * (uint32_t)(CW + 4), bar);
+                bulk_copy_g2s(dst + CW + 4, rp, 16u, bar);
+            } else {
+                bulk_copy_g2s(dst, rp + w0 - 4, 4u * (uint32_t)SW, bar);
+            }
+        }
+        for (int a = 0; a < TR; ++a)
+            bulk_copy_g2s(s_tgt + (size_t)a * CW, tgt + (size_t)(i0 + a) * W + w0, 4u * (uint32_t)CW, bar);
+        return;
+    }
     const int i0 = local_tile * TR;
     const uint32_t* src = d.plane[colour ^ 1];
     const uint32_t* tgt = d.plane[colour];
@@ -224,15 +263,18 @@ __device__ __forceinline__ void store_group(uint32_t* p, const uint32_t v[G])
 // that two 100 KB tile stages and the queues still fit one CTA's shared memory.
 __host__ __device__ constexpr int queue_cap(int threads) { return threads <= 256 ? 160 : 96; }
 
-// Per-tile constants of the word update.
+// Per-tile constants of the word update.  A tile is TR rows of CW words (CW = W:
+// whole rows; else a column block starting at word w0).
 struct TileCtx {
-    const uint32_t* s_src;  // source rows i0 - HB .. i0 + TR + HB - 1 (shared memory)
-    const uint32_t* s_tgt;  // target rows i0 .. i0 + TR - 1 (shared memory)
-    uint32_t* out;          // target plane at row i0 (global memory)
-    uint64_t q_tile;        // Philox call index of the tile's first word: 8 * i0 * W
+    const uint32_t* s_src;  // source rows i0 - HB .. i0 + TR + HB - 1 (shared memory), SW words apart
+    const uint32_t* s_tgt;  // target rows i0 .. i0 + TR - 1 (shared memory), CW words apart
+    uint32_t* out;          // target plane at (row i0, word w0) (global memory)
+    uint64_t q_tile;        // Philox call index of the tile's first word: 8 * (i0 * W + w0)
     uint64_t key;
     uint32_t sweep, t2, t4, all2, all4, zero2, zero4;
     int W, HB, colour;
+    int CW, SW;             // words per tile row; smem source row stride (CW + 8 for column
+                            // blocks, whose rows start with 4 halo words; W for whole rows)
     int par0;               // (i0 + colour) & 1: row i0 + r has its horizontal neighbour on the right iff r + par0 is odd
     bool q_small;           // every call index of the lattice below 2^32
 };
@@ -243,8 +285,9 @@ __device__ __forceinline__ PhiloxWordConsts group_consts(const TileCtx& x, const
 }
 
 // Calls 2..7 for the top n queue entries, one per lane < n (every lane of the warp
-// takes part), then the words' final values and, with COUNT, their counts.
-template <bool COUNT>
+// takes part), then the words' final values and, with COUNT, their counts.  An entry's
+// first field is (row in the tile) << 16 | (word in the tile row).
+template <bool COUNT, bool BLOCKS>
 __device__ __forceinline__ void drain_queue(const TileCtx& x, const PhiloxWordConsts& pc_tile, uint4* wq, int& qn,
                                             int n, int lane, uint32_t& ups, uint32_t& anti)
 {
@@ -255,13 +298,17 @@ __device__ __forceinline__ void drain_queue(const TileCtx& x, const PhiloxWordCo
     __syncwarp();  // entries read before the next pushes overwrite them
     uint32_t und[1] = {e.y}, fm[1] = {e.z};
     const uint32_t sel[1] = {e.w};
-    const uint64_t q = x.q_tile + 8ull * e.x;
+    // whole rows: the entry holds the word's offset from the tile's first word (the same
+    // in the plane and in shared memory); column blocks: (row << 16) | word in the row
+    const uint32_t er = e.x >> 16, ew = e.x & 0xFFFFu;
+    const uint32_t off = BLOCKS ? er * (uint32_t)x.W + ew : e.x;
+    const uint64_t q = x.q_tile + 8ull * off;
     const uint32_t ql[1] = {(uint32_t)q};
     const uint32_t thr[2] = {x.t2, x.t4};
     bitsliced_below<1, 2, 2, 8, true>(und, fm, sel, sel, ql, group_consts(x, pc_tile, q), x.key, thr);
     if (act) {
-        const uint32_t nw = x.s_tgt[e.x] ^ fm[0];
-        x.out[e.x] = nw;
+        const uint32_t nw = x.s_tgt[BLOCKS ? er * (uint32_t)x.CW + ew : e.x] ^ fm[0];
+        x.out[off] = nw;
         if (COUNT) {
             ups += __popc(nw);
             anti += 4u * __popc(fm[0]) - 2u * __popc(fm[0] & sel[0]);
@@ -280,12 +327,15 @@ __device__ __forceinline__ void drain_queue(const TileCtx& x, const PhiloxWordCo
 // __syncwarp).  With COUNT (the colour-1 pass) the counts of flip_masks are added;
 // it is a template parameter so that the colour-0 pass carries none of their
 // instructions (predicated, they cost ~9 % of its issue slots).
-template <int NT, int G, bool COUNT>
+//
+// BLOCKS: the tile is a column block (its source rows carry halo words, so the
+// horizontal neighbours need no wrap); else whole rows (CW = SW = W, wrapped).
+template <int NT, int G, bool COUNT, bool BLOCKS>
 __device__ __forceinline__ void update_tile(const TileCtx& x, const PhiloxWordConsts& pc_tile, int nwords, uint4* wq,
                                             uint32_t& ups, uint32_t& anti)
 {
     const int tid = threadIdx.x, lane = tid & 31;
-    const int W = x.W, WG = W / G, ngroups = nwords / G;
+    const int W = x.W, CW = BLOCKS ? x.CW : W, SW = BLOCKS ? x.SW : W, WG = CW / G, ngroups = nwords / G;
     int qn = 0;  // entries in the warp's queue (the same in every lane)
     // (row, group) of g = tid + k*NT, advanced without a division
     const int step_r = NT / WG, step_w = NT - step_r * WG;
@@ -295,22 +345,22 @@ __device__ __forceinline__ void update_tile(const TileCtx& x, const PhiloxWordCo
         // a lane past the end works on group 0 and keeps nothing
         const bool valid = k0 + tid < ngroups;
         const int rr = valid ? r : 0, w = valid ? wg * G : 0;
-        const uint32_t* srow = x.s_src + (size_t)(x.HB + rr) * W;
+        const uint32_t* srow = x.s_src + (size_t)(x.HB + rr) * SW + (BLOCKS ? 4 : 0);
         uint32_t up[G], dn[G], sm[G], tg[G], hz[G];
-        load_group<G>(srow + w - W, up);
-        load_group<G>(srow + w + W, dn);
+        load_group<G>(srow + w - SW, up);
+        load_group<G>(srow + w + SW, dn);
         load_group<G>(srow + w, sm);
-        load_group<G>(x.s_tgt + (size_t)rr * W + w, tg);
+        load_group<G>(x.s_tgt + (size_t)rr * CW + w, tg);
         if ((rr + x.par0) & 1) {
-            const uint32_t next = srow[(w + G == W) ? 0 : w + G];
+            const uint32_t next = srow[BLOCKS ? w + G : ((w + G == W) ? 0 : w + G)];
 #pragma unroll
             for (int k = 0; k < G; ++k) hz[k] = __funnelshift_r(sm[k], k + 1 < G ? sm[k + 1] : next, 1);
         } else {
-            const uint32_t prev = srow[(w == 0) ? W - 1 : w - 1];
+            const uint32_t prev = srow[BLOCKS ? w - 1 : ((w == 0) ? W - 1 : w - 1)];
 #pragma unroll
             for (int k = 0; k < G; ++k) hz[k] = __funnelshift_l(k > 0 ? sm[k - 1] : prev, sm[k], 1);
         }
-        const uint32_t pos0 = (uint32_t)(rr * W + w);
+        const uint32_t pos0 = (uint32_t)(rr * W + w);  // from the tile's first word, in the plane
         const uint64_t q0 = x.q_tile + 8ull * pos0;  // the group's calls share q's high word
         uint32_t und[G], fm[G], sel[G], ql[G];
 #pragma unroll
@@ -330,7 +380,7 @@ __device__ __forceinline__ void update_tile(const TileCtx& x, const PhiloxWordCo
         // the target words again, so that they need not stay in registers above
         uint32_t nw[G];
         if constexpr (G == 4) {
-            const uint4 tq = ld_shared_v4(x.s_tgt + (size_t)rr * W + w);
+            const uint4 tq = ld_shared_v4(x.s_tgt + (size_t)rr * CW + w);
             nw[0] = tq.x ^ fm[0];
             nw[1] = tq.y ^ fm[1];
             nw[2] = tq.z ^ fm[2];
@@ -348,7 +398,9 @@ __device__ __forceinline__ void update_tile(const TileCtx& x, const PhiloxWordCo
                 anti += 4u * __popc(fm[k]) - 2u * __popc(fm[k] & sel[k]);
             }
             const uint32_t bal = __ballot_sync(0xffffffffu, pend);
-            if (pend) wq[qn + __popc(bal & ((1u << lane) - 1u))] = make_uint4(pos0 + k, und[k], fm[k], sel[k]);
+            if (pend)
+                wq[qn + __popc(bal & ((1u << lane) - 1u))] =
+                    make_uint4(BLOCKS ? ((uint32_t)rr << 16) | (uint32_t)(w + k) : pos0 + k, und[k], fm[k], sel[k]);
             qn += __popc(bal);
             // the drain is inlined at few places: once per group (or per two words in
             // 512-thread CTAs, whose queues are shorter)
@@ -357,7 +409,7 @@ __device__ __forceinline__ void update_tile(const TileCtx& x, const PhiloxWordCo
                 if (qn >= 32) {
                     __syncwarp();  // pushes visible to the draining lanes
                     do {
-                        drain_queue<COUNT>(x, pc_tile, wq, qn, 32, lane, ups, anti);
+                        drain_queue<COUNT, BLOCKS>(x, pc_tile, wq, qn, 32, lane, ups, anti);
                     } while (qn >= 32);
                 }
             }
@@ -371,7 +423,7 @@ __device__ __forceinline__ void update_tile(const TileCtx& x, const PhiloxWordCo
     }
     if (qn > 0) {
         __syncwarp();
-        drain_queue<COUNT>(x, pc_tile, wq, qn, qn, lane, ups, anti);
+        drain_queue<COUNT, BLOCKS>(x, pc_tile, wq, qn, qn, lane, ups, anti);
     }
 }
 
@@ -380,7 +432,11 @@ __device__ __forceinline__ void update_tile(const TileCtx& x, const PhiloxWordCo
 // uniform registers and 2 CTAs of 256 fit at <= 128 registers; the general instance
 // loads them per tile into ordinary registers and is allowed more (one CTA per
 // 256 threads per SM), which is faster than spilling inside the random-number loop.
-template <int NT, bool ONE>
+// TILES as for issue_tile: the single-lattice instance is compiled apart for whole rows
+// (0) and for column blocks (1), and the multi-lattice instance for whole rows (0) and
+// for either (2, once a lattice of the launch has column blocks), so that each carries
+// only the tile code it needs.
+template <int NT, bool ONE, int TILES>
 __global__ void __launch_bounds__(NT, (ONE ? (ISING_SWEEP_THREADS_PER_SM / NT > 0 ? ISING_SWEEP_THREADS_PER_SM / NT : 1)
                                            : (256 / NT > 0 ? 256 / NT : 1)))
     packed_half_sweep_kernel(TileTable tt, const __grid_constant__ LatticeDesc one, int colour, int step,
@@ -398,7 +454,7 @@ __global__ void __launch_bounds__(NT, (ONE ? (ISING_SWEEP_THREADS_PER_SM / NT > 
     uint32_t* stages = reinterpret_cast<uint32_t*>(queues + (NT / 32) * queue_cap(NT));
     const int tid = threadIdx.x;
     const int count = ONE ? 1 : *tt.count;
-    const int total = ONE ? one.L / one.tile_rows : __ldg(tt.tile_start + count);
+    const int total = ONE ? (int)lattice_tiles(one.L, one.tile_rows, one.tile_words) : __ldg(tt.tile_start + count);
 
     // Stage b serves this CTA's tiles tn, tn + 2g, tn + 4g, ... (g = gridDim.x): fill it
     // with the first of them whose lattice is live (tiles of other lattices are skipped:
@@ -408,7 +464,7 @@ __global__ void __launch_bounds__(NT, (ONE ? (ISING_SWEEP_THREADS_PER_SM / NT > 
             const TileInfo ti = tile_info<ONE>(tt, one, count, tn, step);
             if (!ti.live) continue;
             fence_proxy_async_smem();
-            issue_tile(desc_at<ONE>(tt, one, ti.lat), tn - tile_base<ONE>(tt, ti.lat), colour,
+            issue_tile<TILES>(desc_at<ONE>(tt, one, ti.lat), tn - tile_base<ONE>(tt, ti.lat), colour,
                        stages + (size_t)b * stage_words_max, &bars[b], extra_tx);
             return;
         }
@@ -487,14 +543,24 @@ __global__ void __launch_bounds__(NT, (ONE ? (ISING_SWEEP_THREADS_PER_SM / NT > 
                 if (acc_lat >= 0) flush(acc_lat, false);
                 acc_lat = cur.lat;
             }
-            const int W = d.W, L = d.L, TR = d.tile_rows, HB = d.halo_rows;
+            const int W = d.W, L = d.L, TR = d.tile_rows, HB = d.halo_rows, CW = d.tile_words ? d.tile_words : W;
             const uint64_t key = d.key;
             const uint32_t sweep = d.sweep + (uint32_t)step;
             const uint32_t t2 = d.t2, t4 = d.t4, all2 = d.all2, all4 = d.all4;
-            const int i0 = local_tile * TR;
+            // row block and column block of the tile (a single column block of whole rows
+            // when CW == W)
+            const bool blocks = TILES == 1 || (TILES == 2 && CW != W);
+            int i0 = local_tile * TR, w0 = 0;
+            if (blocks) {
+                const int ncb = W / CW;
+                const int rb = local_tile / ncb, cb = local_tile - rb * ncb;
+                i0 = rb * TR;
+                w0 = cb * CW;
+            }
+            const int SW = blocks ? CW + 8 : W;
             uint32_t* out_plane = d.plane[colour];
             const uint32_t* s_src = stages + (size_t)buf * stage_words_max;
-            const uint32_t* s_tgt = s_src + (size_t)(TR + 2 * HB) * W;
+            const uint32_t* s_tgt = s_src + (size_t)(TR + 2 * HB) * SW;
             if (colour == 0 && local_tile == 0 && tid == 0) {
                 // open this sweep's (M, E) slot: M = 2 * ups - N, E = 2 * anti - 2N
                 int64_t* slot = d.hist + 2 * (int64_t)sweep;
@@ -507,8 +573,8 @@ __global__ void __launch_bounds__(NT, (ONE ? (ISING_SWEEP_THREADS_PER_SM / NT > 
             TileCtx x;
             x.s_src = s_src;
             x.s_tgt = s_tgt;
-            x.out = out_plane + (size_t)i0 * W;
-            x.q_tile = 8ull * (uint64_t)i0 * (uint64_t)W;
+            x.out = out_plane + (size_t)i0 * W + w0;
+            x.q_tile = 8ull * ((uint64_t)i0 * (uint64_t)W + (uint64_t)w0);
             x.key = key;
             x.sweep = sweep;
             x.t2 = t2;
@@ -520,25 +586,35 @@ __global__ void __launch_bounds__(NT, (ONE ? (ISING_SWEEP_THREADS_PER_SM / NT > 
             x.W = W;
             x.HB = HB;
             x.colour = colour;
+            x.CW = CW;
+            x.SW = SW;
             x.par0 = (i0 + colour) & 1;
             x.q_small = L <= 131072;
             const PhiloxWordConsts pc_tile = philox_consts(key, 0u, sweep, (uint32_t)colour);
             uint4* wq = queues + (tid >> 5) * queue_cap(NT);
-            const int nwords = TR * W;
+            const int nwords = TR * CW;
             if (colour == 1) {
-                if ((W & 3) == 0)
-                    update_tile<NT, 4, true>(x, pc_tile, nwords, wq, ups, anti);
+                if (TILES != 0 && blocks)
+                    update_tile<NT, 4, true, true>(x, pc_tile, nwords, wq, ups, anti);
+                else if (TILES == 1)
+                    ;
+                else if ((W & 3) == 0)
+                    update_tile<NT, 4, true, false>(x, pc_tile, nwords, wq, ups, anti);
                 else if ((W & 1) == 0)
-                    update_tile<NT, 2, true>(x, pc_tile, nwords, wq, ups, anti);
+                    update_tile<NT, 2, true, false>(x, pc_tile, nwords, wq, ups, anti);
                 else
-                    update_tile<NT, 1, true>(x, pc_tile, nwords, wq, ups, anti);
+                    update_tile<NT, 1, true, false>(x, pc_tile, nwords, wq, ups, anti);
             } else {
-                if ((W & 3) == 0)
-                    update_tile<NT, 4, false>(x, pc_tile, nwords, wq, ups, anti);
+                if (TILES != 0 && blocks)
+                    update_tile<NT, 4, false, true>(x, pc_tile, nwords, wq, ups, anti);
+                else if (TILES == 1)
+                    ;
+                else if ((W & 3) == 0)
+                    update_tile<NT, 4, false, false>(x, pc_tile, nwords, wq, ups, anti);
                 else if ((W & 1) == 0)
-                    update_tile<NT, 2, false>(x, pc_tile, nwords, wq, ups, anti);
+                    update_tile<NT, 2, false, false>(x, pc_tile, nwords, wq, ups, anti);
                 else
-                    update_tile<NT, 1, false>(x, pc_tile, nwords, wq, ups, anti);
+                    update_tile<NT, 1, false, false>(x, pc_tile, nwords, wq, ups, anti);
             }
             // this warp is done with the stage; the last warp to be done refills it
             __syncwarp();
@@ -577,31 +653,37 @@ int packed_smem_header_bytes(int threads)
 
 template <int NT>
 void launch_nt(const TileTable& tt, const LatticeDesc* one, int colour, int step, int* status, int grid, size_t smem,
-               int stage_words, cudaStream_t s, long long wait_limit, uint32_t extra_tx)
+               int stage_words, cudaStream_t s, long long wait_limit, uint32_t extra_tx, bool blocks)
 {
-    if (one)
-        packed_half_sweep_kernel<NT, true><<<grid, NT, smem, s>>>(tt, *one, colour, step, status, stage_words,
-                                                                  wait_limit, extra_tx);
+    if (one && one->tile_words != 0 && one->tile_words != one->W)
+        packed_half_sweep_kernel<NT, true, 1><<<grid, NT, smem, s>>>(tt, *one, colour, step, status, stage_words,
+                                                                     wait_limit, extra_tx);
+    else if (one)
+        packed_half_sweep_kernel<NT, true, 0><<<grid, NT, smem, s>>>(tt, *one, colour, step, status, stage_words,
+                                                                     wait_limit, extra_tx);
+    else if (blocks)
+        packed_half_sweep_kernel<NT, false, 2><<<grid, NT, smem, s>>>(tt, LatticeDesc{}, colour, step, status,
+                                                                      stage_words, wait_limit, extra_tx);
     else
-        packed_half_sweep_kernel<NT, false><<<grid, NT, smem, s>>>(tt, LatticeDesc{}, colour, step, status,
-                                                                   stage_words, wait_limit, extra_tx);
+        packed_half_sweep_kernel<NT, false, 0><<<grid, NT, smem, s>>>(tt, LatticeDesc{}, colour, step, status,
+                                                                      stage_words, wait_limit, extra_tx);
 }
 
 cudaError_t launch_packed_half_sweep(const TileTable& tt, int colour, int step, int* status, int grid, int threads,
                                      int smem_stage_bytes, cudaStream_t s, long long wait_limit, uint32_t extra_tx,
-                                     const LatticeDesc* one)
+                                     const LatticeDesc* one, bool blocks)
 {
     const int stage_words = smem_stage_bytes / 4;
     const size_t smem = (size_t)packed_smem_header_bytes(threads) + 2 * (size_t)smem_stage_bytes;
     switch (threads) {
     case 128:
-        launch_nt<128>(tt, one, colour, step, status, grid, smem, stage_words, s, wait_limit, extra_tx);
+        launch_nt<128>(tt, one, colour, step, status, grid, smem, stage_words, s, wait_limit, extra_tx, blocks);
         break;
     case 256:
-        launch_nt<256>(tt, one, colour, step, status, grid, smem, stage_words, s, wait_limit, extra_tx);
+        launch_nt<256>(tt, one, colour, step, status, grid, smem, stage_words, s, wait_limit, extra_tx, blocks);
         break;
     case 512:
-        launch_nt<512>(tt, one, colour, step, status, grid, smem, stage_words, s, wait_limit, extra_tx);
+        launch_nt<512>(tt, one, colour, step, status, grid, smem, stage_words, s, wait_limit, extra_tx, blocks);
         break;
     default:
         return cudaErrorInvalidValue;
@@ -612,11 +694,18 @@ cudaError_t launch_packed_half_sweep(const TileTable& tt, int colour, int step, 
 template <int NT>
 cudaError_t set_limit_nt(size_t bytes)
 {
-    cudaError_t e = cudaFuncSetAttribute(packed_half_sweep_kernel<NT, false>,
+    cudaError_t e = cudaFuncSetAttribute(packed_half_sweep_kernel<NT, false, 2>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(packed_half_sweep_kernel<NT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)bytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(packed_half_sweep_kernel<NT, false, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)bytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(packed_half_sweep_kernel<NT, true, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)bytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(packed_half_sweep_kernel<NT, true, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)bytes);
+    return e;
 }
 
 cudaError_t packed_set_smem_limit(int threads, size_t bytes)
@@ -636,9 +725,15 @@ cudaError_t packed_set_smem_limit(int threads, size_t bytes)
 template <int NT>
 cudaError_t occupancy_nt(size_t smem, int* blocks_per_sm, bool one)
 {
-    return one ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, packed_half_sweep_kernel<NT, true>, NT, smem)
-               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, packed_half_sweep_kernel<NT, false>, NT,
-                                                               smem);
+    // the lower of the instance's two builds
+    int a = 0, b = 0;
+    cudaError_t e = one ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, packed_half_sweep_kernel<NT, true, 0>, NT, smem)
+                        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, packed_half_sweep_kernel<NT, false, 0>, NT, smem);
+    if (e == cudaSuccess)
+        e = one ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, packed_half_sweep_kernel<NT, true, 1>, NT, smem)
+                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, packed_half_sweep_kernel<NT, false, 2>, NT, smem);
+    *blocks_per_sm = a < b ? a : b;
+    return e;
 }
 
 cudaError_t packed_occupancy(int threads, size_t smem, int* blocks_per_sm, bool one)

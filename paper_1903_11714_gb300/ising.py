@@ -43,6 +43,7 @@ _SIGS = {
     "ising_history": (ctypes.c_int, [_vp, _i64, _i64, _P(_i64), _P(_i64)]),
     "ising_moments": (ctypes.c_int, [_vp, _i64, _P(_d), _P(_u64)]),
     "ising_get_lattice": (ctypes.c_int, [_vp, _P(ctypes.c_int8)]),
+    "ising_get_rows": (ctypes.c_int, [_vp, _i64, _i64, _P(ctypes.c_int8)]),
     "ising_set_lattice": (ctypes.c_int, [_vp, _P(ctypes.c_int8)]),
     "ising_get_planes": (ctypes.c_int, [_vp, _P(ctypes.c_uint32), _P(ctypes.c_uint32)]),
     "ising_set_planes": (ctypes.c_int, [_vp, _P(ctypes.c_uint32), _P(ctypes.c_uint32)]),
@@ -55,6 +56,7 @@ _SIGS = {
     "ising_init3d": (ctypes.c_int, [_P(_vp), _i64, _d, _u64, ctypes.c_int, _vp]),
     "ising_batch_create": (ctypes.c_int, [_P(_vp), _i32, _i64, _i64, _i32, _vp]),
     "ising_batch_add": (ctypes.c_int, [_vp, _i64, _d, _u64, _i32, _i64, _i32, _P(_i32)]),
+    "ising_batch_add_tiled": (ctypes.c_int, [_vp, _i64, _d, _u64, _i32, _i64, _i32, _i32, _P(_i32)]),
     "ising_batch_remove": (ctypes.c_int, [_vp, _i32]),
     "ising_batch_run": (ctypes.c_int, [_vp, _i64, _i32]),
     "ising_batch_sweeps_done": (ctypes.c_int, [_vp, _i32, _P(_i64)]),
@@ -200,6 +202,13 @@ def ising_get_lattice(h: int, L: int, dim: int = 2) -> np.ndarray:
     return out
 
 
+def ising_get_rows(h: int, L: int, row0: int, nrows: int) -> np.ndarray:
+    """Rows row0 .. row0+nrows-1 as an (nrows, L) int8 array (a cube's rows are r = i*L + j)."""
+    out = np.empty((int(nrows), L), dtype=np.int8)
+    _check(lib().ising_get_rows(h, int(row0), int(nrows), _ptr(out, ctypes.c_int8)))
+    return out
+
+
 def ising_set_lattice(h: int, lattice: np.ndarray) -> None:
     a = np.ascontiguousarray(lattice, dtype=np.int8)
     _check(lib().ising_set_lattice(h, _ptr(a, ctypes.c_int8)))
@@ -309,6 +318,9 @@ class Lattice:
     def get_lattice(self) -> np.ndarray:
         return ising_get_lattice(self.h, self.L)
 
+    def get_rows(self, row0: int, nrows: int) -> np.ndarray:
+        return ising_get_rows(self.h, self.L, row0, nrows)
+
     def set_lattice(self, a: np.ndarray) -> None:
         ising_set_lattice(self.h, a)
 
@@ -357,10 +369,11 @@ class Batch:
         self.b = b.value
         self.L = {}
 
-    def add(self, L: int, beta: float, seed: int, start: int, sweeps: int, tile_rows: int = 0) -> int:
+    def add(self, L: int, beta: float, seed: int, start: int, sweeps: int, tile_rows: int = 0,
+            tile_words: int = 0) -> int:
         idx = ctypes.c_int32()
-        _check(lib().ising_batch_add(self.b, int(L), float(beta), int(seed), int(start), int(sweeps),
-                                     int(tile_rows), ctypes.byref(idx)))
+        _check(lib().ising_batch_add_tiled(self.b, int(L), float(beta), int(seed), int(start), int(sweeps),
+                                           int(tile_rows), int(tile_words), ctypes.byref(idx)))
         self.L[idx.value] = int(L)
         return idx.value
 
@@ -437,6 +450,9 @@ class Lattice3D(Lattice):
 
     def get_lattice(self) -> np.ndarray:
         return ising_get_lattice(self.h, self.L, dim=3)
+
+    def get_rows(self, row0: int, nrows: int) -> np.ndarray:
+        return ising_get_rows(self.h, self.L, row0, nrows)
 
     def set_lattice(self, a: np.ndarray) -> None:
         raise IsingError(ISING_EINVAL, "set_lattice is for 2D lattices; use set_planes")

@@ -74,9 +74,9 @@ def test_thresholds_reject_bad_beta(lib, beta):
 
 @pytest.mark.parametrize("L,kernel", [(0, ising.PACKED), (96, ising.PACKED), (32, ising.PACKED),
                                       (12, ising.INT8), (4, ising.INT8), (2**21, ising.PACKED),
-                                      # rows too long for a double-buffered shared-memory tile:
-                                      # above 272,896 (L % 256 == 0) or 102,336 (otherwise)
-                                      (272_896 + 256, ising.PACKED), (102_336 + 128, ising.PACKED),
+                                      # above 2^20, or rows too long for a whole-row tile when
+                                      # L % 256 != 0 (no column blocks then): above 102,336
+                                      ((1 << 20) + 256, ising.PACKED), (102_336 + 128, ising.PACKED),
                                       (185_408, ising.PACKED)])
 def test_init_rejects_bad_sizes_before_device_work(lib, L, kernel):
     with pytest.raises(ising.IsingError) as e:
