@@ -554,6 +554,10 @@ def main() -> None:
     ap.add_argument("--workload", choices=["single_large", "single_small", "scan", "uneven", "serve", "binder",
                                            "cubic", "binder3d"],
                     default="single_large")
+    ap.add_argument("--config", type=int, choices=[1, 2, 3, 4, 5], default=0,
+                    help="the five benchmark configurations: 1 = L=128 single (single_small), "
+                         "2 = L=65,536 single (single_large), 3 = temperature scan (scan), "
+                         "4 = uneven batch (uneven), 5 = serving loop (serve)")
     ap.add_argument("--binder-sweeps", type=int, default=1_000_000)
     ap.add_argument("--binder3d-sweeps", type=int, default=100_000)
     ap.add_argument("--serve-requests", type=int, default=2000)
@@ -562,6 +566,8 @@ def main() -> None:
     ap.add_argument("--serve-quantum", type=int, default=32)
     ap.add_argument("--serve-budget-gb", type=float, default=120.0)
     args = ap.parse_args()
+    if args.config:
+        args.workload = {1: "single_small", 2: "single_large", 3: "scan", 4: "uneven", 5: "serve"}[args.config]
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     rank, world, local = dist_env()

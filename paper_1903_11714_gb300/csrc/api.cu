@@ -54,7 +54,6 @@ constexpr int64_t kPackedMaxL = 1 << 20;
 constexpr int64_t kInt8MaxL = 1 << 17;
 constexpr uint32_t kNoTarget = 0xFFFFFFFFu;
 constexpr int64_t kMaxSweeps = 0xFFFFFFFEll;  // sweep counter is a 32-bit Philox counter word
-constexpr int64_t kStageCapBytes = 100 * 1024;  // per pipeline stage (two stages per CTA)
 
 // Handle kind of a cubic (3D) lattice; the public kernel ids are ISING_PACKED
 // and ISING_INT8 (2D).

@@ -57,6 +57,9 @@ __host__ __device__ inline int64_t lattice_tiles(int64_t L, int32_t tile_rows, i
     return (L / tile_rows) * (W / (tile_words ? tile_words : W));
 }
 
+// Largest shared-memory stage of the tiled sweep (two stages per CTA).
+constexpr int64_t kStageCapBytes = 100 * 1024;
+
 // Bound on every mbarrier wait of the sweep kernel, in SM clocks (~2 s at 2 GHz,
 // far beyond any tile copy).  After it the kernel records kStatusTimeout and
 // its CTAs return.
@@ -108,6 +111,10 @@ void set_last_error(const char* msg);
 
 // Packed sweep kernel configuration helpers (sweep_packed.cu).
 int packed_smem_header_bytes(int threads);
+// Allows launches with up to max(bytes, header + 2 stages of kStageCapBytes) of dynamic
+// shared memory on every instance of the sweep kernel for `threads`.  The limit is
+// per kernel, shared by every engine of the process, so it is never set below the
+// largest launch any engine can make.
 cudaError_t packed_set_smem_limit(int threads, size_t bytes);
 // Resident CTAs per SM of the sweep kernel: the single-lattice instance (one) or
 // the general one, which the two launch bounds give different register budgets.

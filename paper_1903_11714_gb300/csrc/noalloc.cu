@@ -29,7 +29,7 @@ namespace {
 constexpr int kNoAllocMaxLattices = 64;
 constexpr int kNoAllocThreads = 256;
 constexpr int kNoAllocMaxDevices = 64;
-constexpr int64_t kNoAllocStageCap = 100 * 1024;  // same per-stage limit as the handle API
+constexpr int64_t kNoAllocStageCap = kStageCapBytes;  // the handle API's per-stage limit
 
 struct NoAllocScratch {
     LatticeDesc desc[kNoAllocMaxLattices];

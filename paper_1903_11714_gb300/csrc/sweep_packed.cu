@@ -694,6 +694,8 @@ cudaError_t launch_packed_half_sweep(const TileTable& tt, int colour, int step, 
 template <int NT>
 cudaError_t set_limit_nt(size_t bytes)
 {
+    const size_t most = (size_t)packed_smem_header_bytes(NT) + 2 * (size_t)kStageCapBytes;
+    if (bytes < most) bytes = most;
     cudaError_t e = cudaFuncSetAttribute(packed_half_sweep_kernel<NT, false, 2>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e == cudaSuccess)

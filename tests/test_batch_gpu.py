@@ -191,3 +191,25 @@ def test_autotune_returns_a_valid_tile():
     for L in (64, 1024, 4096):
         tr, th, ms = ising.ising_autotune(L)
         assert tr in (2, 4, 8, 16, 32, 64, 128, 256) and L % tr == 0 and th in (256, 512) and ms > 0
+
+
+def test_batch_still_runs_after_a_smaller_engine_is_configured():
+    """Engines share the sweep kernel's shared-memory limit: a single handle with small
+    tiles created after a batch with large ones must not lower it below the batch's
+    launches."""
+    beta = 0.4406868
+    b = ising.Batch(2, 8192, 1 << 30, 0)
+    k = b.add(8192, beta, 3, ising.HOT, 8, 64)   # 64-row tiles of 128-word rows: a large stage
+    b.run(2)
+    b.synchronize()
+    small = ising.Lattice(512, beta, 4, ising.HOT).sweep(2)  # configures a small engine
+    small.close()
+    b.run(2)
+    b.synchronize()
+    assert b.sweeps_done(k) == 4
+    M, E = b.history(k, 0, 4)
+    lat = ising.Lattice(8192, beta, 3, ising.HOT).sweep(4)
+    Ms, Es = lat.history()
+    assert np.array_equal(M, Ms) and np.array_equal(E, Es)
+    lat.close()
+    b.close()

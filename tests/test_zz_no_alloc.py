@@ -67,3 +67,49 @@ def test_noalloc_refuses_more_lattices_than_its_scratch_holds():
         ising.ising_sweep_packed_noalloc([1] * n, [1] * n, [64] * n, [0.4] * n, [1] * n, 0, 1, [1] * n)
     assert e.value.code == ising.ISING_EINVAL
     assert "64" in ising.last_error()
+
+
+def test_noalloc_writes_stay_inside_the_planes():
+    """Guard words around caller-owned planes and M/E arrays (one buffer per lattice:
+    guard, black plane, guard, white plane, guard, M/E, guard) keep their canary value
+    after sweeps of every row width class (W % 4 == 0, odd, 2 mod 4), and the swept
+    lattices still equal the handle API's."""
+    import torch
+
+    libbuild.build()
+    G, CANARY, n = 1024, 0x5A5A5A5A, 4
+    specs = [(256, 0.4406868, 7, ising.HOT), (192, 0.3, 8, ising.HOT), (128, 0.5, 10, ising.COLD),
+             (1024, 0.55, 9, ising.COLD)]
+    bufs, layout, handles = [], [], []
+    for L, beta, seed, start in specs:
+        pw = L * (L // 64)
+        h = ising.Lattice(L, beta, seed, start, ising.PACKED)
+        b, w = h.get_planes()
+        buf = torch.full((4 * G + 2 * pw + 4 * n,), CANARY, dtype=torch.int32)
+        ob, ow, om = G, 2 * G + pw, 3 * G + 2 * pw
+        buf[ob:ob + pw] = torch.from_numpy(b.view(np.int32))
+        buf[ow:ow + pw] = torch.from_numpy(w.view(np.int32))
+        buf[om:om + 4 * n] = 0
+        bufs.append(buf.cuda())
+        layout.append((pw, ob, ow, om))
+        handles.append(h)
+    torch.cuda.synchronize()
+    ptr = lambda k, off: bufs[k].data_ptr() + 4 * off
+    ising.ising_sweep_packed_noalloc([ptr(k, l[1]) for k, l in enumerate(layout)],
+                                     [ptr(k, l[2]) for k, l in enumerate(layout)],
+                                     [s[0] for s in specs], [s[1] for s in specs], [s[2] for s in specs],
+                                     first_sweep=0, nsweeps=n,
+                                     me_ptrs=[ptr(k, l[3]) for k, l in enumerate(layout)], wait=True)
+    torch.cuda.synchronize()
+    for k, (h, (pw, ob, ow, om)) in enumerate(zip(handles, layout)):
+        got = bufs[k].cpu()
+        guards = torch.cat([got[:G], got[ob + pw:ow], got[ow + pw:om], got[om + 4 * n:]])
+        assert bool((guards == CANARY).all()), f"lattice {k}: a guard word was written"
+        h.sweep(n)
+        hb, hw = h.get_planes()
+        assert np.array_equal(got[ob:ob + pw].numpy().view(np.uint32), hb), k
+        assert np.array_equal(got[ow:ow + pw].numpy().view(np.uint32), hw), k
+        me = got[om:om + 4 * n].numpy().view(np.int64)
+        M, E = h.history()
+        assert np.array_equal(me[0::2], M) and np.array_equal(me[1::2], E), k
+        h.close()
