@@ -161,7 +161,8 @@ __device__ __forceinline__ int tile_base(const TileTable& tt, int lat)
         return __ldg(tt.tile_start + lat);
 }
 
-// Thread 0: stage the tile's rows.  Source rows [i0 - HB, i0 + TR + HB) (wrapped)
+// One thread (thread 0 for the first two tiles, afterwards lane 0 of the last warp to
+// release the stage) stages the tile's rows.  Source rows [i0 - HB, i0 + TR + HB) (wrapped)
 // and target rows [i0, i0 + TR).  Every copy starts on a 16-byte boundary: with
 // W % 4 == 0 every row does (TR may then be 2); otherwise HB = 4 and tiles start
 // on rows that are multiples of 4, so each copied block starts at a multiple of

@@ -14,9 +14,10 @@ namespace ising {
 // its threshold from the top bit down decides the site at the first plane where
 // the two bits differ: U < T there iff the threshold's bit is 1.  Per plane and
 // word that is four logic operations for all 32 sites; planes are drawn four at a
-// time (one Philox call) and drawing stops once no site of the thread's words is
-// undecided -- on average after about three of the eight calls, against eight
-// calls for whole 32-bit uniforms.  The decisions are those of the full 32-bit
+// time (one Philox call) and drawing stops once no site is undecided -- a word alone
+// needs about two of its eight calls (the tiled kernels draw calls 0-1 in step with
+// the warp and finish the ~10 % of words with sites left from a queue), against
+// eight calls for whole 32-bit uniforms.  The decisions are those of the full 32-bit
 // comparison, bit for bit.
 //
 // und[k]: sites of word k still to test (updated); lt[k]: sites found below their
