@@ -180,7 +180,7 @@ def committed_counters(kernel: str):
             "capture": d.get("command")}
 
 
-def issue_roofline(kernel: str, sites_per_launch: float, t_launch_s: float, sm_max: float, peaks: dict) -> dict:
+def kernel_roofline(kernel: str, sites_per_launch: float, t_launch_s: float, sm_max: float, peaks: dict) -> dict:
     """Roofline of one half-sweep launch.  The binding unit is the ALU pipe (16 lanes x 4
     schedulers per SM; the busiest pipe in the committed ncu counters), so `achieved` is
     the launch's ALU-pipe thread operations (ncu sm__inst_executed_pipe_alu.sum x 32,
@@ -401,7 +401,7 @@ def run_cubic(args) -> None:
     lat.close()
     value = steps * N / (ms * 1e6)
     t_launch_s = ms * 1e-3 / (2 * steps)
-    roofline = issue_roofline("cubic_half_sweep", N / 2, t_launch_s, sm_max, peaks)
+    roofline = kernel_roofline("cubic_half_sweep", N / 2, t_launch_s, sm_max, peaks)
     cpu = None
     if not args.no_cpu_baseline:
         cpu = cubic_cpu_baseline(cfg.beta, cfg.seed)
@@ -644,7 +644,7 @@ def main() -> None:
     launches = 2 * args.steps + 1
     t_launch_s = ms * 1e-3 / (2 * args.steps)
     if kernel == ising.PACKED:
-        roofline = issue_roofline("packed_half_sweep", N / 2, t_launch_s, sm_max, peaks)
+        roofline = kernel_roofline("packed_half_sweep", N / 2, t_launch_s, sm_max, peaks)
     else:
         roofline = {"bound": "alu", "achieved": None, "peak": None, "unit": "Tinst/s", "frac": None, "traffic": None,
                     "hbm_achieved_gbs": 2.0 * N / t_launch_s / 1e9, "hbm_peak_gbs": peaks.get("hbm_gbs", 6800.0),
