@@ -34,7 +34,7 @@ def lib():
     return ising.lib()
 
 
-def test_header_declares_the_survey_boundary():
+def test_header_declares_the_boundary_entry_points():
     names = header_functions()
     for required in ("ising_init", "ising_sweep", "ising_observables", "ising_history", "ising_moments",
                      "ising_get_lattice", "ising_set_lattice", "ising_thresholds", "ising_free",
