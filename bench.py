@@ -276,7 +276,8 @@ def _events(torch, stream):
 
 
 def run_single_small(args) -> None:
-    """L = 128, 1000 sweeps, packed vs plain int8 (launch-latency bound)."""
+    """L = 128, 1000 sweeps: packed (one resident CTA for all sweeps, bound by that
+    one SM) vs plain int8 (two launches per sweep, launch-latency bound)."""
     import torch
 
     from paper_1903_11714_gb300 import ising, workloads
@@ -298,7 +299,7 @@ def run_single_small(args) -> None:
         out[name] = cfg.sweeps * cfg.L ** 2 / (ms * 1e6)
     print(json.dumps({"metric": "spin-flip attempts/ns, L=128 single lattice", "workload": "single_small",
                       "unit": UNIT, "value": out["packed"], "int8_value": out["int8"],
-                      "config": cfg.as_dict(), "note": "2 kernel launches per sweep; launch-latency bound"}))
+                      "config": cfg.as_dict(), "note": "packed: one single-CTA launch for all sweeps; int8: 2 launches per sweep (launch-latency bound)"}))
 
 
 def run_batched(args, which: str) -> None:

@@ -8,6 +8,13 @@
 namespace ising {
 namespace {
 
+// Philox calls drawn side by side for every word with sites to test, before the
+// rest are drawn one at a time (Sec. 3.1 acceptance on the bit planes of
+// philox.cuh): a warp runs a call while any of its lanes needs it, and nearly every
+// warp needs its words' first three, so drawing them together adds almost no issue
+// slots and overlaps their latencies.
+constexpr int kFirstCalls = 3;  // 9.2 flips/ns at L = 128 (8.9 with 2, 8.7 one call at a time)
+
 // Resident form for one small lattice: both planes live in this CTA's shared
 // memory for `nsweeps` sweeps, with a block barrier between half-sweeps instead
 // of a kernel launch.  Same words, neighbours, draws and decisions as the tiled
@@ -28,6 +35,9 @@ __global__ void __launch_bounds__(NT, 1) packed_resident_kernel(const __grid_con
     __syncthreads();
     const uint64_t key = d.key;
     const bool q_small = L <= 131072;
+    // thresholds 0 (never accept) are taken out of the test like 2^32 (always)
+    const uint32_t zero2 = (d.t2 == 0u && d.all2 == 0u) ? ~0u : 0u, zero4 = (d.t4 == 0u && d.all4 == 0u) ? ~0u : 0u;
+    const uint32_t thr[2] = {d.t2, d.t4};
     for (int s = 0; s < nsweeps; ++s) {
         const uint32_t sweep = d.sweep + (uint32_t)s;
         for (int colour = 0; colour < 2; ++colour) {
@@ -48,14 +58,30 @@ __global__ void __launch_bounds__(NT, 1) packed_resident_kernel(const __grid_con
                 const PhiloxWordConsts pc =
                     q_small ? pc_all : philox_consts(key, (uint32_t)(q0 >> 32), sweep, (uint32_t)colour);
                 const uint32_t tw = tgt[idx];
-                uint32_t f[1];
-                {
-                    const uint32_t t1[1] = {tw};
-                    const uint32_t u1[1] = {up}, d1[1] = {down}, m1[1] = {same}, z1[1] = {hz}, ql[1] = {(uint32_t)q0};
-                    if (colour == 1)
-                        flip_masks<1, true>(t1, u1, d1, m1, z1, ql, pc, key, d.t2, d.t4, d.all2, d.all4, f, ups, anti);
-                    else
-                        flip_masks<1, false>(t1, u1, d1, m1, z1, ql, pc, key, d.t2, d.t4, d.all2, d.all4, f, ups, anti);
+                uint32_t f[1], und[1], sel[1], anti0;
+                classify_word(tw, up, down, same, hz, d.all2, d.all4, zero2, zero4, f[0], und[0], sel[0], anti0);
+                if (und[0] != 0u) {
+                    // calls 0 .. kFirstCalls-1 side by side, then one at a time while needed
+                    uint32_t b[kFirstCalls], o[kFirstCalls][4];
+#pragma unroll
+                    for (int c = 0; c < kFirstCalls; ++c) b[c] = ((uint32_t)q0 ^ pc.x0k) ^ (uint32_t)c;
+                    philox_calls<kFirstCalls>(b, 0u, pc, key, o);
+#pragma unroll
+                    for (int c = 0; c < kFirstCalls; ++c)
+#pragma unroll
+                        for (int m = 0; m < 4; ++m) {
+                            const int bit = 31 - (4 * c + m);
+                            const uint32_t tm = (sel[0] & (0u - ((d.t2 >> bit) & 1u))) | (~sel[0] & (0u - ((d.t4 >> bit) & 1u)));
+                            const uint32_t x = und[0] & (o[c][m] ^ tm);  // decided in this plane
+                            f[0] |= x & tm;                             // ... below: U's bit 0, T's bit 1
+                            und[0] &= ~x;
+                        }
+                    const uint32_t ql[1] = {(uint32_t)q0};
+                    bitsliced_below<1, 2, kFirstCalls, 8>(und, f, sel, sel, ql, pc, key, thr);
+                }
+                if (colour == 1) {
+                    ups += __popc(same);
+                    anti += anti0 + 4u * __popc(f[0]) - 2u * __popc(f[0] & sel[0]);
                 }
                 tgt[idx] = tw ^ f[0];
                 if (colour == 1) ups += __popc(tw ^ f[0]);
