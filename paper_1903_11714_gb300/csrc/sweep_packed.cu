@@ -325,8 +325,9 @@ __device__ __forceinline__ void drain_queue(const TileCtx& x, const PhiloxWordCo
 // word per lane.  So the rare long comparisons no longer hold a whole warp, which
 // draws about 2.2 calls per word instead of the ~3.4 a warp-wide early exit needs.
 // A queued word is stored twice: as far as decided, then final (ordered by
-// __syncwarp).  With COUNT (the colour-1 pass) the counts of flip_masks are added;
-// it is a template parameter so that the colour-0 pass carries none of their
+// __syncwarp).  With COUNT (the colour-1 pass) the fused M/E counts are added (the
+// bond count from the adder bits, derived in word_update.cuh); COUNT is a template
+// parameter so that the colour-0 pass carries none of their
 // instructions (predicated, they cost ~9 % of its issue slots).
 //
 // BLOCKS: the tile is a column block (its source rows carry halo words, so the
