@@ -13,6 +13,8 @@
 * The energy carried incrementally (+2h per accepted flip) equals the energy
   recomputed from scratch after every half-sweep.
 * Lattice invariants and the light-cone window evaluation.
+* The Sec. 4.1 moments (|m|, m^2, m^4, e, U4) on sample sets with closed-form
+  moments: binomial M at beta = 0, ordered chains, a three-point distribution.
 """
 import math
 
@@ -280,3 +282,67 @@ def test_moments_exact_against_float():
     assert r["m2"] == pytest.approx((m ** 2).mean(), rel=1e-13)
     assert r["binder"] == pytest.approx(1 - (m ** 4).mean() / (3 * (m ** 2).mean() ** 2), rel=1e-12)
     assert r["e"] == pytest.approx(E[50:].mean() / N, rel=1e-13)
+
+
+def test_moments_match_closed_forms():
+    """moments_exact on sample sets whose moments are known in closed form, so that a
+    wrong power of N, a dropped absolute value or a wrong constant in U4 fails:
+
+    * every configuration of N = 16 independent +-1 spins once (beta = 0): M = 2k - N
+      with binomial weights, <M^2> = N, <M^4> = 3N^2 - 2N, hence U4 = 2/(3N);
+      <|M|> = N C(N, N/2) / 2^N (the mean distance of a simple random walk after N
+      steps); E summed over all states is 0 (each bond product is a fair +-1);
+    * an ordered chain, M = +-N: |m| = m^2 = m^4 = 1 and U4 = 2/3;
+    * m in {0, +a, -a} with weights 2:1:1: <m^2> = a^2/2, <m^4> = a^4/2, U4 = 1/3;
+    * burn-in drops exactly the first samples; a common factor of M and N leaves the
+      magnetisation moments unchanged; sums stay exact at |M| = 2^32 (M^4 = 2^128).
+    """
+    from fractions import Fraction
+
+    N = 16
+    x = np.arange(1 << N, dtype=np.uint32)
+    k = np.zeros_like(x)
+    for b in range(N):
+        k += (x >> np.uint32(b)) & np.uint32(1)
+    M = 2 * k.astype(np.int64) - N
+    E = np.zeros_like(M)
+    r = oracle.moments_exact(M, E, N, 0)
+    assert r["n"] == 1 << N
+    assert r["m2"] == float(Fraction(N, N * N))
+    assert r["m4"] == float(Fraction(3 * N * N - 2 * N, N ** 4))
+    assert r["binder"] == float(Fraction(2, 3 * N))
+    assert r["abs_m"] == float(Fraction(N * math.comb(N, N // 2), (1 << N) * N))
+    assert r["e"] == 0.0
+    # the 4x4 torus at beta = 0: each of the 2N bond products is +-1 with equal weight
+    s = np.where(((x[:, None] >> np.arange(N, dtype=np.uint32)) & 1) == 1, 1, -1).reshape(-1, 4, 4)
+    E_torus = -(s * np.roll(s, 1, axis=1) + s * np.roll(s, 1, axis=2)).sum(axis=(1, 2))
+    assert oracle.moments_exact(M, E_torus, N, 0)["e"] == 0.0
+    assert oracle.moments_exact(M, E_torus, N, 0)["e2"] == float(Fraction(2 * N, N * N))
+
+    L = 64
+    Nl = L * L
+    ordered = np.array([Nl, -Nl] * 20, dtype=np.int64)
+    r = oracle.moments_exact(ordered, np.full(40, -2 * Nl), Nl, 0)
+    assert (r["abs_m"], r["m2"], r["m4"], r["binder"], r["e"]) == (1.0, 1.0, 1.0, float(Fraction(2, 3)), -2.0)
+
+    a = 1024
+    three = np.array([0, 0, a, -a] * 25, dtype=np.int64)
+    r = oracle.moments_exact(three, np.zeros(100, dtype=np.int64), Nl, 0)
+    assert r["binder"] == float(Fraction(1, 3))
+    assert r["m2"] == float(Fraction(a * a, 2 * Nl * Nl))
+    assert r["abs_m"] == float(Fraction(a, 2 * Nl))
+
+    rng = np.random.default_rng(3)
+    seq = rng.integers(-Nl, Nl + 1, size=300)
+    eseq = rng.integers(-2 * Nl, 2 * Nl + 1, size=300)
+    junk = rng.integers(-Nl, Nl + 1, size=7)
+    base = oracle.moments_exact(seq, eseq, Nl, 0)
+    assert oracle.moments_exact(np.concatenate([junk, seq]), np.concatenate([junk, eseq]), Nl, 7) == base
+    scaled = oracle.moments_exact(3 * seq, eseq, 3 * Nl, 0)
+    for key in ("abs_m", "m2", "m4", "binder"):
+        assert scaled[key] == base[key], key
+
+    big = np.array([1 << 32, -(1 << 32), 1 << 31], dtype=object)
+    r = oracle.moments_exact(big, [0, 0, 0], 1 << 32, 0)
+    assert r["S4"] == 2 * (1 << 128) + (1 << 124)
+    assert r["m4"] == float(Fraction(2 * 16 + 1, 3 * 16))
