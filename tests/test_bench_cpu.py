@@ -1,0 +1,71 @@
+"""Host arithmetic of bench.py's roofline object (CPU, no GPU).
+
+* The counter records are tied to the kernel sources by a hash of the code
+  without comments, so a comment edit keeps a record current and a code edit
+  makes it stale (string literals, which hold inline PTX, count as code).
+* `achieved` = ALU-pipe thread operations per site x sites per launch / launch
+  time, against 64 lanes per clock per SM x 152 SMs x the SM clock; `traffic` is
+  the record's DRAM bytes per site x sites, and null once the record is stale.
+"""
+import json
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+
+def test_code_only_drops_comments_and_keeps_strings():
+    a = 'int x = 1; // one\n/* block\n comment */ asm("add.u32 %0, %1; // kept");\n'
+    b = 'int   x = 1;\n asm("add.u32 %0, %1; // kept");'
+    assert bench.code_only(a) == bench.code_only(b)
+    assert "// kept" in bench.code_only(a)
+    assert bench.code_only(a) != bench.code_only(a.replace("x = 1", "x = 2"))
+    assert bench.code_only(a) != bench.code_only(a.replace("add.u32", "sub.u32"))
+
+
+@pytest.mark.parametrize("kernel", sorted(bench.KERNEL_SOURCES))
+def test_every_counter_record_names_its_capture(kernel):
+    with open(os.path.join(ROOT, "profiles", f"{kernel}_counters.json")) as f:
+        d = json.load(f)
+    assert d["kernel"] == kernel
+    assert "--clock-control none" in d["command"]
+    assert len(d["kernel_source_hash"]) == 16
+    c = bench.committed_counters(kernel)
+    assert c is not None and c["alu_ops_per_site"] > 0 and c["inst_slots_per_site"] >= c["alu_ops_per_site"]
+
+
+def fake_counters(current):
+    return {"current": current, "inst_slots_per_site": 6.0, "alu_ops_per_site": 3.5,
+            "dram_bytes_per_site": 0.4, "capture": "ncu ..."}
+
+
+def test_roofline_arithmetic(monkeypatch):
+    monkeypatch.setattr(bench, "committed_counters", lambda k: fake_counters(True))
+    sites, t, mhz = 2.0 ** 31, 6.0e-4, 2070.0
+    r = bench.kernel_roofline("packed_half_sweep", sites, t, mhz, {"hbm_gbs": 6778.7})
+    peak = 64 * 152 * mhz * 1e6 / 1e12
+    assert r["bound"] == "alu" and r["unit"] == "Tops/s"
+    assert r["peak"] == pytest.approx(peak) and r["peak"] == pytest.approx(20.137, abs=1e-3)
+    assert r["achieved"] == pytest.approx(3.5 * sites / t / 1e12)
+    assert r["frac"] == pytest.approx(r["achieved"] / peak)
+    assert r["traffic"] == pytest.approx(0.4 * sites)
+    assert r["counters"] == "current"
+    assert r["issue_view"]["peak"] == pytest.approx(2 * peak)
+    assert r["issue_view"]["achieved"] == pytest.approx(6.0 * sites / t / 1e12)
+    # the HBM view: 0.375 algorithmic bytes per updated site of a half-sweep (= per site and sweep)
+    assert r["hbm_achieved_gbs"] == pytest.approx(0.375 * sites / t / 1e9)
+    assert r["hbm_peak_gbs"] == 6778.7
+
+
+def test_stale_counters_null_the_traffic(monkeypatch):
+    monkeypatch.setattr(bench, "committed_counters", lambda k: fake_counters(False))
+    r = bench.kernel_roofline("packed_half_sweep", 1e6, 1e-5, 2070.0, {})
+    assert r["traffic"] is None and r["counters"].startswith("stale")
+    monkeypatch.setattr(bench, "committed_counters", lambda k: None)
+    r = bench.kernel_roofline("packed_half_sweep", 1e6, 1e-5, 2070.0, {})
+    assert r["achieved"] is None and r["frac"] is None and r["traffic"] is None
