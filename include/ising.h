@@ -160,7 +160,10 @@ int ising_set_planes(ising_t h, const uint32_t *black, const uint32_t *white);
 /*
  * Checkpoint: ising_state_bytes gives the size of the blob; ising_save writes
  * (L, beta, seed, kernel, sweeps done, lattice, history) into buf; ising_load
- * creates a new handle that continues the same chain bit for bit.
+ * creates a new handle that continues the same chain bit for bit.  ising_load
+ * returns ISING_EINVAL, before creating any handle or device memory, for a
+ * buffer that is not a checkpoint, is shorter than its header says, or whose
+ * kernel, start or sweep count is out of range; *out is then left unchanged.
  */
 int ising_state_bytes(ising_t h, int64_t *bytes);
 int ising_save(ising_t h, void *buf, int64_t bytes);

@@ -1054,6 +1054,16 @@ int ising_load(ising_t* out, const void* buf, int64_t bytes, void* stream)
     CkptHeader hd;
     memcpy(&hd, buf, sizeof(hd));
     if (memcmp(hd.magic, "ISINGCK1", 8) != 0 || hd.version != 1) return fail(ISING_EINVAL, "not a checkpoint");
+    // header fields checked before any device work, so that a damaged blob can
+    // neither allocate nor size a copy past the end of buf (16 * sweeps_done and
+    // lattice_bytes stay far below 2^63 once these hold)
+    if (hd.kernel != ISING_PACKED && hd.kernel != ISING_INT8 && hd.kernel != kKernelCubic)
+        return fail(ISING_EINVAL, "checkpoint kernel out of range");
+    if (hd.start != ISING_HOT && hd.start != ISING_COLD) return fail(ISING_EINVAL, "checkpoint start out of range");
+    if (hd.sweeps_done < 0 || hd.sweeps_done > kMaxSweeps)
+        return fail(ISING_EINVAL, "checkpoint sweep count out of range");
+    if (hd.lattice_bytes < 0 || hd.lattice_bytes > bytes - (int64_t)sizeof(CkptHeader))
+        return fail(ISING_EINVAL, "checkpoint truncated");
     ising_t h = nullptr;
     int rc = hd.kernel == kKernelCubic ? ising_init3d(&h, hd.L, hd.beta, hd.seed, ISING_COLD, stream)
                                        : ising_init_ex(&h, hd.L, hd.beta, hd.seed, ISING_COLD, (int)hd.kernel, stream);

@@ -119,3 +119,38 @@ def test_null_handles_are_rejected(lib):
 
 def test_version_string(lib):
     assert "sm_103a" in lib.ising_version().decode()
+
+
+def checkpoint_header(L=128, kernel=ising.PACKED, start=ising.HOT, sweeps_done=0, lattice_bytes=None,
+                      magic=b"ISINGCK1", version=1, beta=0.44, seed=1):
+    """The 72-byte checkpoint header of ising_save: magic, then version, L, kernel,
+    start, sweeps done and lattice bytes (int64), beta (double), seed (uint64)."""
+    import struct
+    if lattice_bytes is None:
+        lattice_bytes = L * L if kernel == ising.INT8 else L * L // 8
+    return struct.pack("<8s6qdQ", magic, version, L, kernel, start, sweeps_done, lattice_bytes, beta, seed)
+
+
+@pytest.mark.parametrize("fields,extra", [
+    (dict(magic=b"ISINGCK2"), 4096),
+    (dict(version=2), 4096),
+    (dict(kernel=7), 4096),
+    (dict(kernel=-1), 4096),
+    (dict(start=5), 4096),
+    (dict(sweeps_done=-1), 4096),             # would size a negative history copy
+    (dict(sweeps_done=1 << 40), 4096),        # beyond the 32-bit sweep counter
+    (dict(sweeps_done=(1 << 63) // 16), 4096),  # 16 * sweeps_done wraps a 64-bit size
+    (dict(lattice_bytes=-8), 4096),
+    (dict(lattice_bytes=1 << 62), 4096),
+    (dict(), 100),                            # planes of 2 KB cut short
+])
+def test_damaged_checkpoints_are_rejected_before_device_work(lib, fields, extra):
+    """A damaged header is refused with EINVAL before any handle or device memory
+    exists (on a machine without a GPU, reaching the device would report ECUDA)."""
+    blob = checkpoint_header(**fields) + bytes(extra)
+    buf = ctypes.create_string_buffer(blob, len(blob))
+    h = ctypes.c_void_p()
+    rc = lib.ising_load(ctypes.byref(h), buf, len(blob), None)
+    assert rc == ising.ISING_EINVAL, (fields, rc, lib.ising_last_error())
+    assert h.value is None
+    assert lib.ising_load(ctypes.byref(h), buf, 40, None) == ising.ISING_EINVAL
