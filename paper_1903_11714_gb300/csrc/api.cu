@@ -802,7 +802,7 @@ int ising_sweep(ising_t h, int64_t n)
     int rc = check_handle(h);
     if (rc) return rc;
     if (n < 0) return fail(ISING_EINVAL, "n must be >= 0");
-    if (h->sweeps_done + n > kMaxSweeps) return fail(ISING_EINVAL, "sweep counter would pass 2^32 - 2");
+    if (n > kMaxSweeps - h->sweeps_done) return fail(ISING_EINVAL, "sweep counter would pass 2^32 - 2");
     if (n == 0) return ISING_OK;
     rc = ensure_hist(h, h->sweeps_done + n);
     if (rc) return rc;
@@ -874,7 +874,7 @@ int ising_history(ising_t h, int64_t first, int64_t count, int64_t* M, int64_t* 
 {
     int rc = check_handle(h);
     if (rc) return rc;
-    if (first < 0 || count < 0 || first + count > h->sweeps_done)
+    if (first < 0 || count < 0 || first > h->sweeps_done || count > h->sweeps_done - first)
         return fail(ISING_EINVAL, "history range [%lld, %lld) beyond %lld sweeps", (long long)first,
                     (long long)(first + count), (long long)h->sweeps_done);
     std::vector<int64_t> buf(2 * (size_t)count);
@@ -1327,7 +1327,8 @@ int ising_batch_history(ising_batch_t b, int32_t idx, int64_t first, int64_t cou
     int64_t done = 0;
     rc = batch_sweeps_done(b, idx, &done);
     if (rc) return rc;
-    if (first < 0 || count < 0 || first + count > done) return fail(ISING_EINVAL, "history range beyond sweeps done");
+    if (first < 0 || count < 0 || first > done || count > done - first)
+        return fail(ISING_EINVAL, "history range beyond sweeps done");
     std::vector<int64_t> buf(2 * (size_t)count);
     const auto& d = b->slots[idx].desc;
     if (count) CK(cudaMemcpyAsync(buf.data(), d.hist + 2 * first, sizeof(int64_t) * buf.size(),

@@ -132,7 +132,7 @@ extern "C" int ising_sweep_packed_noalloc(int32_t count, uint32_t* const* black,
         return set_error(ISING_EINVAL, buf);
     }
     if (!black || !white || !L || !beta || !seed || !me) return set_error(ISING_EINVAL, "null argument");
-    if (first_sweep < 0 || nsweeps < 0 || first_sweep + nsweeps > 0xFFFFFFFEll)
+    if (first_sweep < 0 || nsweeps < 0 || first_sweep > 0xFFFFFFFEll || nsweeps > 0xFFFFFFFEll - first_sweep)
         return set_error(ISING_EINVAL, "sweep range outside 0 .. 2^32 - 2");
     SetupParams p;
     memset(&p, 0, sizeof(p));

@@ -148,6 +148,10 @@ def test_sweep_limits_stop_each_lattice():
     assert b.sweeps_done(i0) == 7 and b.sweeps_done(i1) == 20
     ref, Mr, _, _ = oracle.run(256, 0.44, 1, oracle.HOT, 7)
     assert np.array_equal(b.get_lattice(i0), ref) and np.array_equal(b.history(i0)[0], Mr)
+    # history ranges whose end wraps a signed 64-bit integer are refused before any copy
+    big = (1 << 63) - 3
+    assert ising.lib().ising_batch_history(b.b, i0, big, 5, None, None) == ising.ISING_EINVAL
+    assert ising.lib().ising_batch_history(b.b, i0, 2, big, None, None) == ising.ISING_EINVAL
     b.close()
 
 

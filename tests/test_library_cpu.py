@@ -154,3 +154,21 @@ def test_damaged_checkpoints_are_rejected_before_device_work(lib, fields, extra)
     assert rc == ising.ISING_EINVAL, (fields, rc, lib.ising_last_error())
     assert h.value is None
     assert lib.ising_load(ctypes.byref(h), buf, 40, None) == ising.ISING_EINVAL
+
+
+@pytest.mark.parametrize("first,n", [(-1, 1), (0, -1), (0xFFFFFFFE, 1), (1, 0xFFFFFFFE),
+                                     (1 << 62, 1 << 62), ((1 << 63) - 10, 20)])
+def test_noalloc_sweep_range_is_checked_before_device_work(lib, first, n):
+    """Sweep numbers must stay in 0 .. 2^32 - 2 (the 32-bit Philox sweep word);
+    ranges whose end passes it -- including sums that wrap a signed 64-bit integer --
+    are refused with EINVAL before any device work (which here would give ECUDA)."""
+    vp1 = ctypes.c_void_p * 1
+    planes = (ctypes.c_uint32 * 2048)()
+    me = (ctypes.c_int64 * 64)()
+    black = vp1(ctypes.cast(planes, ctypes.c_void_p))
+    mes = vp1(ctypes.cast(me, ctypes.c_void_p))
+    L = (ctypes.c_int64 * 1)(256)
+    beta = (ctypes.c_double * 1)(0.44)
+    seed = (ctypes.c_uint64 * 1)(1)
+    rc = lib.ising_sweep_packed_noalloc(1, black, black, L, beta, seed, first, n, mes, None, 0)
+    assert rc == ising.ISING_EINVAL, (first, n, rc, lib.ising_last_error())

@@ -222,6 +222,15 @@ def test_history_range_errors():
         lat.history(3, 5)
     with pytest.raises(ising.IsingError):
         lat.moments(5)
+    # ranges and sweep counts whose sums wrap a signed 64-bit integer are refused
+    # before any copy or launch
+    big = (1 << 63) - 3
+    lib = ising.lib()
+    assert lib.ising_history(lat.h, big, 5, None, None) == ising.ISING_EINVAL
+    assert lib.ising_history(lat.h, 2, big, None, None) == ising.ISING_EINVAL
+    assert lib.ising_sweep(lat.h, (1 << 63) - 1) == ising.ISING_EINVAL
+    assert lib.ising_sweep(lat.h, 0xFFFFFFFE - 4) == ising.ISING_EINVAL
+    assert lat.observables()[2] == 5
     lat.close()
 
 
