@@ -4,7 +4,10 @@
   include/ising.h declares (and the binding binds exactly those).
 * ising_thresholds (host-only) equals the oracle's independently written
   thresholds bit for bit (the FP64 libm reading of the acceptance rule).
-* Argument validation rejects bad input before touching the device.
+* Argument validation rejects bad input before touching the device, including
+  damaged checkpoint headers and ranges whose sums would wrap.
+* Without a device the product path reports ISING_ECUDA (there is no CPU
+  fallback), and a missing library is an error.
 """
 import ctypes
 import os
@@ -172,3 +175,23 @@ def test_noalloc_sweep_range_is_checked_before_device_work(lib, first, n):
     seed = (ctypes.c_uint64 * 1)(1)
     rc = lib.ising_sweep_packed_noalloc(1, black, black, L, beta, seed, first, n, mes, None, 0)
     assert rc == ising.ISING_EINVAL, (first, n, rc, lib.ising_last_error())
+
+
+def test_product_path_fails_loudly_without_a_device(lib):
+    """No CPU fallback: where there is no GPU, creating a lattice or a batch reports
+    the CUDA failure instead of running the sweep anywhere else."""
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    for make in (lambda: ising.Lattice(128, 0.44, 1), lambda: ising.Lattice(128, 0.44, 1, ising.HOT, ising.INT8),
+                 lambda: ising.Lattice3D(64, 0.22, 1), lambda: ising.Batch(2, 256, 1 << 20)):
+        with pytest.raises(ising.IsingError) as e:
+            make()
+        assert e.value.code == ising.ISING_ECUDA
+
+
+def test_missing_library_is_an_error(monkeypatch, tmp_path):
+    monkeypatch.setattr(ising, "_lib", None)
+    monkeypatch.setattr(ising, "LIB_PATH", str(tmp_path / "libising_gb300.so"))
+    with pytest.raises(RuntimeError, match="missing"):
+        ising.lib()
