@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "ising.h"
+#include "arena.h"
 #include "ising_internal.cuh"
 #include "sweep3d.cuh"
 
@@ -349,53 +350,16 @@ int make_stream(void* user, cudaStream_t* s, bool* own)
 }
 
 // ---------------------------------------------------------------- arena
-// First-fit sub-allocator over one device region: the batch's HBM budget.
-struct Arena {
+// First-fit sub-allocator over one device region: the batch's HBM budget.  The
+// offsets are kept by FreeList (arena.h); this adds the region.
+struct Arena : FreeList {
     char* base = nullptr;
-    int64_t size = 0;
-    int64_t used = 0;
-    std::map<int64_t, int64_t> free_;  // offset -> length
 
     int init(int64_t bytes)
     {
-        size = (bytes + 255) / 256 * 256;
+        reset(bytes);
         CK(cudaMalloc(&base, (size_t)size));
-        free_.clear();
-        free_[0] = size;
-        used = 0;
         return ISING_OK;
-    }
-    int64_t alloc(int64_t bytes)
-    {
-        bytes = (bytes + 255) / 256 * 256;
-        for (auto it = free_.begin(); it != free_.end(); ++it) {
-            if (it->second >= bytes) {
-                const int64_t off = it->first, len = it->second;
-                free_.erase(it);
-                if (len > bytes) free_[off + bytes] = len - bytes;
-                used += bytes;
-                return off;
-            }
-        }
-        return -1;
-    }
-    void release(int64_t off, int64_t bytes)
-    {
-        bytes = (bytes + 255) / 256 * 256;
-        used -= bytes;
-        auto it = free_.emplace(off, bytes).first;
-        auto nx = std::next(it);
-        if (nx != free_.end() && it->first + it->second == nx->first) {
-            it->second += nx->second;
-            free_.erase(nx);
-        }
-        if (it != free_.begin()) {
-            auto pv = std::prev(it);
-            if (pv->first + pv->second == it->first) {
-                pv->second += it->second;
-                free_.erase(it);
-            }
-        }
     }
     void destroy()
     {
