@@ -195,3 +195,44 @@ def test_missing_library_is_an_error(monkeypatch, tmp_path):
     monkeypatch.setattr(ising, "LIB_PATH", str(tmp_path / "libising_gb300.so"))
     with pytest.raises(RuntimeError, match="missing"):
         ising.lib()
+
+
+def no_device_or_skip(lib):
+    """The size sweeps below rely on accepted sides failing at the first device call;
+    where a device answers, they would allocate up to 128 GB, so they skip."""
+    h = ctypes.c_void_p()
+    rc = lib.ising_init_ex(ctypes.byref(h), 64, 0.44, 1, ising.HOT, ising.PACKED, None)
+    if rc == ising.ISING_OK:
+        lib.ising_free(h)
+    if rc != ising.ISING_ECUDA:
+        pytest.skip("a device is present")
+
+
+def test_accepted_sides_are_exactly_the_documented_ones(lib):
+    """Every side up past each limit: EINVAL (before device work) exactly where
+    include/ising.h says the side is outside the kernel's range; any other side gets
+    as far as the device (ECUDA here).  Packed: L % 64 == 0, 64 <= L, and L <= 2^20
+    when L % 256 == 0, else L <= 102,336.  int8: L % 8 == 0, 8 <= L <= 131,072.
+    Cubic: L % 64 == 0, 64 <= L <= 8,192."""
+    no_device_or_skip(lib)
+    h = ctypes.c_void_p()
+
+    def packed_ok(L):
+        return L % 64 == 0 and L >= 64 and (L <= 1 << 20 if L % 256 == 0 else L <= 102_336)
+
+    def int8_ok(L):
+        return L % 8 == 0 and 8 <= L <= 131_072
+
+    def cubic_ok(L):
+        return L % 64 == 0 and 64 <= L <= 8192
+
+    cases = [(ising.PACKED, packed_ok, list(range(-64, (1 << 20) + 2048, 32)) + [65, 100, 102_400 + 1]),
+             (ising.INT8, int8_ok, list(range(-8, 131_072 + 256, 4)) + [9, 130_000 + 1])]
+    for kernel, ok, sides in cases:
+        for L in sides:
+            rc = lib.ising_init_ex(ctypes.byref(h), L, 0.44, 1, ising.HOT, kernel, None)
+            assert rc == (ising.ISING_ECUDA if ok(L) else ising.ISING_EINVAL), (kernel, L, rc)
+    for L in list(range(-64, 8192 + 1024, 32)) + [65, 1 << 20]:
+        rc = lib.ising_init3d(ctypes.byref(h), L, 0.22, 1, ising.HOT, None)
+        assert rc == (ising.ISING_ECUDA if cubic_ok(L) else ising.ISING_EINVAL), ("cubic", L, rc)
+    assert h.value is None
