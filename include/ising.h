@@ -217,6 +217,8 @@ int ising_init3d(ising_t *out, int64_t L, double beta, uint64_t seed, int start,
  * max_L with `arena_bytes` of device memory for planes and histories (the HBM
  * budget; allocation beyond it is ENOMEM).  threads: CTA size of the sweep
  * kernel (128, 256 or 512; 0 = 256).  stream as in ising_init_ex.
+ * EINVAL, before any device work, unless 1 <= capacity <= 2^20, max_L is a
+ * multiple of 64 in 64 .. 2^20 and arena_bytes >= 256.
  */
 int ising_batch_create(ising_batch_t *out, int32_t capacity, int64_t max_L, int64_t arena_bytes, int32_t threads,
                        void *stream);

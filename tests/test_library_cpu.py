@@ -236,3 +236,53 @@ def test_accepted_sides_are_exactly_the_documented_ones(lib):
         rc = lib.ising_init3d(ctypes.byref(h), L, 0.22, 1, ising.HOT, None)
         assert rc == (ising.ISING_ECUDA if cubic_ok(L) else ising.ISING_EINVAL), ("cubic", L, rc)
     assert h.value is None
+
+
+def test_batch_create_arguments(lib):
+    """ising_batch_create: EINVAL unless 1 <= capacity <= 2^20, max_L a multiple of 64
+    in 64 .. 2^20, threads in {0, 128, 256, 512} and arena_bytes >= 256; valid
+    arguments get as far as the device."""
+    no_device_or_skip(lib)
+    b = ctypes.c_void_p()
+    good = dict(capacity=4, max_L=1024, arena=1 << 20, threads=0)
+    bad = [dict(capacity=0), dict(capacity=(1 << 20) + 1), dict(max_L=0), dict(max_L=100), dict(max_L=32),
+           dict(max_L=(1 << 20) + 64), dict(threads=64), dict(threads=300), dict(threads=1024), dict(arena=255)]
+    for change in bad + [dict()] + [dict(threads=t) for t in (128, 256, 512)] + [dict(max_L=1 << 20, capacity=1 << 20)]:
+        a = {**good, **change}
+        rc = lib.ising_batch_create(ctypes.byref(b), a["capacity"], a["max_L"], a["arena"], a["threads"], None)
+        assert rc == (ising.ISING_EINVAL if change in bad else ising.ISING_ECUDA), (change, rc)
+    assert b.value is None
+
+
+def test_noalloc_lattice_arguments(lib):
+    """ising_sweep_packed_noalloc: per-lattice sides as documented (L % 64 == 0,
+    64 <= L, L <= 163,840 when L % 256 == 0, else L <= 102,336), finite beta >= 0,
+    non-null pointers and 1 <= count <= 64 -- all checked before device work."""
+    no_device_or_skip(lib)
+    vp = ctypes.c_void_p
+    buf = (ctypes.c_uint32 * 16)()
+    p = ctypes.cast(buf, vp)
+
+    def call(Ls, betas=None, count=None, null_plane=False):
+        n = len(Ls)
+        planes = (vp * n)(*([None] if null_plane else []) + [p] * (n - int(null_plane)))
+        mes = (vp * n)(*[p] * n)
+        Larr = (ctypes.c_int64 * n)(*Ls)
+        barr = (ctypes.c_double * n)(*(betas or [0.44] * n))
+        sarr = (ctypes.c_uint64 * n)(*range(n))
+        return lib.ising_sweep_packed_noalloc(n if count is None else count, planes, planes, Larr, barr, sarr,
+                                             0, 1, mes, None, 0)
+
+    def ok(L):
+        return L % 64 == 0 and L >= 64 and (L <= 163_840 if L % 256 == 0 else L <= 102_336)
+
+    for L in list(range(-64, 200_000, 32)) + [1 << 20, (1 << 20) + 64]:
+        assert call([L]) == (ising.ISING_ECUDA if ok(L) else ising.ISING_EINVAL), L
+    assert call([256, 100]) == ising.ISING_EINVAL          # any bad lattice refuses the call
+    for beta in (float("nan"), float("inf"), -0.1):
+        assert call([256], betas=[beta]) == ising.ISING_EINVAL
+    assert call([256], betas=[0.0]) == ising.ISING_ECUDA
+    assert call([256, 512], null_plane=True) == ising.ISING_EINVAL
+    assert call([256], count=0) == ising.ISING_EINVAL
+    assert call([256] * 65) == ising.ISING_EINVAL
+    assert call([256] * 64) == ising.ISING_ECUDA
