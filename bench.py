@@ -553,7 +553,7 @@ def run_serve(args) -> None:
                       "blocked_by_memory": summ["blocked_by_memory"], "blocked_by_slots": summ["blocked_by_slots"]}))
 
 
-def main() -> None:
+def make_parser() -> argparse.ArgumentParser:
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=200)
@@ -578,7 +578,11 @@ def main() -> None:
     ap.add_argument("--serve-slots", type=int, default=256)
     ap.add_argument("--serve-quantum", type=int, default=32)
     ap.add_argument("--serve-budget-gb", type=float, default=120.0)
-    args = ap.parse_args()
+    return ap
+
+
+def main() -> None:
+    args = make_parser().parse_args()
     if args.config:
         args.workload = {1: "single_small", 2: "single_large", 3: "scan", 4: "uneven", 5: "serve"}[args.config]
     if args.warmup < 3 and args.impl == "ours":

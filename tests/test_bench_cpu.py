@@ -69,3 +69,32 @@ def test_stale_counters_null_the_traffic(monkeypatch):
     monkeypatch.setattr(bench, "committed_counters", lambda k: None)
     r = bench.kernel_roofline("packed_half_sweep", 1e6, 1e-5, 2070.0, {})
     assert r["achieved"] is None and r["frac"] is None and r["traffic"] is None
+
+
+def profile_commands():
+    """Command lines in profiles/*.md (backslash continuations joined)."""
+    out = []
+    pdir = os.path.join(ROOT, "profiles")
+    for name in sorted(os.listdir(pdir)):
+        if not name.endswith(".md"):
+            continue
+        text = open(os.path.join(pdir, name)).read().replace("\\\n", " ")
+        for line in text.splitlines():
+            line = line.split("#")[0].strip().strip("`")
+            if line.startswith(("ncu ", "python bench.py")):
+                out.append((name, line))
+    return out
+
+
+def test_profile_commands_still_run_as_written():
+    """Each summary's commands run committed files only: bench.py with options it
+    still accepts, and every ncu with --clock-control none."""
+    cmds = profile_commands()
+    assert {n for n, _ in cmds} == {f for f in os.listdir(os.path.join(ROOT, "profiles")) if f.endswith(".md")}
+    for name, line in cmds:
+        assert "_work" not in line, (name, line)
+        if line.startswith("ncu "):
+            assert "--clock-control none" in line, (name, line)
+            assert "python bench.py" in line, (name, line)
+        argv = line.split("python bench.py", 1)[1].split()
+        bench.make_parser().parse_args(argv)
