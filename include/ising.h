@@ -323,15 +323,23 @@ int ising_dev_philox(uint64_t key, const uint32_t ctr[4], int64_t nblocks, uint3
  * otherwise (4-row tiles must fit a 100 KB stage); beta[k] finite and >= 0; seed[k] its Philox key;
  * me[k] a device array of 2*nsweeps int64 that receives (M, E) after each of the
  * sweeps first_sweep .. first_sweep+nsweeps-1 (M at [2s], E at [2s+1], s counted
- * from first_sweep).  The host arrays black, white, L, beta, seed, me are read
- * during the call only.  The chain is the one ising_sweep produces: calling with
- * first_sweep = n continues n sweeps done earlier, bit for bit.
+ * from first_sweep).  me[k] need not be cleared: each sweep overwrites its pair
+ * (the black half-sweep stores the pair's starting value, the white half-sweep adds
+ * the counts), whatever the array held before.  The host arrays black, white, L,
+ * beta, seed, me are read during the call only.  The chain is the one ising_sweep
+ * produces: calling with first_sweep = n continues n sweeps done earlier, bit for
+ * bit.  The sweep numbers (and so the random numbers) of a call are fixed by its
+ * first_sweep: work enqueued by one call always repeats sweeps first_sweep ..
+ * first_sweep+nsweeps-1, and a chain goes on only through a call with the next
+ * first_sweep.
  *
  * Work is enqueued on `stream` (a cudaStream_t; NULL = legacy default stream).
  * wait != 0: the call synchronises the stream and returns ISING_ETIMEOUT if a
- * bounded wait in the sweep kernel expired; wait == 0: it returns at once.
+ * bounded wait in the sweep kernel expired (ISING_ECUDA for any other status the
+ * kernel reports); a stream that is being captured cannot be synchronised, so
+ * wait != 0 on one is ISING_EINVAL before any work.  wait == 0: it returns at once.
  *
- * Scratch (descriptors, tile table, status word, ~4.4 KB) is a file-scope
+ * Scratch (64 descriptors, tile table, count and status word: 5,392 bytes) is a file-scope
  * __device__ array that every GPU loading this library holds until exit; no
  * call allocates or frees device memory.  The first call on a device looks up
  * that array's address (cudaGetSymbolAddress) and sets the kernel's

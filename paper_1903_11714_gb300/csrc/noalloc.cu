@@ -37,6 +37,10 @@ struct NoAllocScratch {
     int32_t count;
     int32_t status;
 };
+// The size the header states (64 descriptors of 80 bytes, the tile table, count and
+// status: 5,388 bytes, padded to 5,392).
+static_assert(sizeof(LatticeDesc) == 80, "descriptor size behind the stated scratch size");
+static_assert(sizeof(NoAllocScratch) == 5392, "scratch size stated in the header");
 
 // The scratch of every call.  In host code `g_noalloc_scratch` names a host-side
 // shadow, not device memory; host code must use the address that
@@ -170,6 +174,13 @@ extern "C" int ising_sweep_packed_noalloc(int32_t count, uint32_t* const* black,
         if (tiles > 0x7FFFFFFF) return set_error(ISING_EINVAL, "too many tiles");
         p.tile_start[k + 1] = (int32_t)tiles;
     }
+    if (wait) {
+        // a stream that is being captured cannot be synchronised; refuse before any work
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        cudaError_t ce = cudaStreamIsCapturing((cudaStream_t)stream, &cs);
+        if (ce != cudaSuccess) return set_error(ISING_ECUDA, cudaGetErrorString(ce));
+        if (cs != cudaStreamCaptureStatusNone) return set_error(ISING_EINVAL, "wait != 0 on a stream that is being captured");
+    }
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return set_error(ISING_ECUDA, cudaGetErrorString(e));
@@ -204,7 +215,12 @@ extern "C" int ising_sweep_packed_noalloc(int32_t count, uint32_t* const* black,
         e = cudaMemcpyAsync(&host_status, status, sizeof(int), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return set_error(ISING_ECUDA, cudaGetErrorString(e));
-        if (host_status != kStatusOk) return set_error(ISING_ETIMEOUT, "sweep kernel's bounded wait expired");
+        if (host_status == kStatusTimeout) return set_error(ISING_ETIMEOUT, "sweep kernel's bounded wait expired");
+        if (host_status != kStatusOk) {
+            char buf[96];
+            snprintf(buf, sizeof(buf), "sweep kernel reported status %d (a bad tile or descriptor)", host_status);
+            return set_error(ISING_ECUDA, buf);
+        }
     }
     return ISING_OK;
 }

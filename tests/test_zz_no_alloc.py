@@ -7,7 +7,8 @@ bit planes and the M/E output array, and the sweep kernel's scratch lives in a
 fixed file-scope device array inside the library.  This test checks, through
 the C ABI, that two calls in a row reproduce exactly what the handle API
 (ising_init_ex + ising_sweep) computes -- the same lattices and the same
-per-sweep M and E -- and that a call with too many lattices is refused.
+per-sweep M and E, written over M/E arrays that start as garbage -- and that a
+call with too many lattices is refused.
 It is collected last so that a failure here stops a -x run only after every
 other test has run.
 """
@@ -21,6 +22,7 @@ pytestmark = pytest.mark.gpu
 
 SPECS = [(256, 0.4406868, 7, ising.HOT), (192, 0.3, 8, ising.HOT), (1024, 0.55, 9, ising.COLD)]
 N_SWEEPS = 6
+GARBAGE = 0x123456789ABCDEF
 
 
 def test_two_noalloc_calls_match_the_handle_api():
@@ -33,8 +35,9 @@ def test_two_noalloc_calls_match_the_handle_api():
         b, w = h.get_planes()  # start state, host copy
         black.append(torch.from_numpy(b.view(np.int32)).cuda())
         white.append(torch.from_numpy(w.view(np.int32)).cuda())
-        me1.append(torch.zeros(2 * N_SWEEPS, dtype=torch.int64, device="cuda"))
-        me2.append(torch.zeros(2 * N_SWEEPS, dtype=torch.int64, device="cuda"))
+        # the M/E arrays start as garbage: every sweep must overwrite its pair, not add to it
+        me1.append(torch.full((2 * N_SWEEPS,), GARBAGE, dtype=torch.int64, device="cuda"))
+        me2.append(torch.full((2 * N_SWEEPS,), -GARBAGE, dtype=torch.int64, device="cuda"))
         handles.append(h)
     torch.cuda.synchronize()
     args = dict(black_ptrs=[t.data_ptr() for t in black], white_ptrs=[t.data_ptr() for t in white],
