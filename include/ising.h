@@ -86,10 +86,13 @@ int ising_thresholds(double beta, uint64_t T[2]);
  * Creates a lattice of side L at inverse temperature beta with Philox seed
  * `seed`: hot start, bit-packed kernel, default stream.  Equivalent to
  * ising_init_ex(out, L, beta, seed, ISING_HOT, ISING_PACKED, NULL).
+ * Paper: Sec. 3 (the L x L torus, H with mu = 0, J = 1, inverse temperature beta).
  */
 int ising_init(ising_t *out, int64_t L, double beta, uint64_t seed);
 
 /*
+ * Paper: Sec. 3 (the torus and H), Sec. 3.2 (the lattice held as compact colour
+ * sub-lattices, here bit planes).
  * start: ISING_HOT or ISING_COLD.  kernel: ISING_PACKED (L % 64 == 0, 64 <= L <=
  * 1048576 when L % 256 == 0 -- rows longer than 4,264 words are swept in 2-row
  * column blocks -- else L <= 102336, so that a double-buffered tile of whole rows
@@ -102,6 +105,8 @@ int ising_init(ising_t *out, int64_t L, double beta, uint64_t seed);
 int ising_init_ex(ising_t *out, int64_t L, double beta, uint64_t seed, int start, int kernel, void *stream);
 
 /*
+ * Paper: Sec. 3.1 (one sweep = the black then the white half of the checkerboard
+ * kernel, each site flipped with probability min{1, exp(-2 beta h)}).
  * Enqueues n sweeps (n >= 0) on the handle's stream; returns without waiting.
  * The sweep counter advances by n (total must stay below 2^32 - 1) and the
  * per-sweep (M, E) history grows by n entries.  Errors: EINVAL, ENOMEM, ECUDA.
@@ -109,6 +114,7 @@ int ising_init_ex(ising_t *out, int64_t L, double beta, uint64_t seed, int start
 int ising_sweep(ising_t h, int64_t n);
 
 /*
+ * Paper: Sec. 4.1 (magnetisation) and Sec. 3 (E = H(sigma)).
  * Current M and E (after the last sweep; the start state if none) and the
  * number of sweeps done.  Synchronises.  Any output pointer may be NULL.
  * Errors: EINVAL, ECUDA, ETIMEOUT.
@@ -116,6 +122,7 @@ int ising_sweep(ising_t h, int64_t n);
 int ising_observables(ising_t h, int64_t *M, int64_t *E, int64_t *sweeps_done);
 
 /*
+ * Paper: Sec. 4.1 (one (M, E) sample per sweep, the series its moments average).
  * Copies history entries first .. first+count-1 (sweep indices, 0-based) into
  * the caller's arrays M[count] and E[count] (either may be NULL).  Synchronises.
  * Errors: EINVAL (range beyond sweeps done), ECUDA, ETIMEOUT.
@@ -123,16 +130,25 @@ int ising_observables(ising_t h, int64_t *M, int64_t *E, int64_t *sweeps_done);
 int ising_history(ising_t h, int64_t first, int64_t count, int64_t *M, int64_t *E);
 
 /*
- * Sec. 4.1 observables over samples s = burn_in .. sweeps_done-1, from exact
- * integer sums on the device: out[0] = <|m|>, out[1] = <m^2>, out[2] = <m^4>,
- * out[3] = <e> (E/N), out[4] = <e^2>, out[5] = U4 = 1 - <m^4>/(3 <m^2>^2).
+ * Sec. 4.1 observables over samples s = burn_in .. sweeps_done-1 (the paper drops
+ * the first 10 % as burn-in), from exact integer sums on the device, evaluated in
+ * FP64 once: *abs_m = <|m|>, *m2 = <m^2>, *m4 = <m^4>, *e = <e> (E/N) and
+ * *binder = U4 = 1 - <m^4>/(3 <m^2>^2), m = M/N.  Any output may be NULL.
+ * Synchronises.  Errors: EINVAL (null handle, no samples after burn_in), ECUDA.
+ */
+int ising_moments(ising_t h, int64_t burn_in, double *abs_m, double *m2, double *m4, double *e, double *binder);
+
+/*
+ * As ising_moments, with <e^2> and the exact sums as well: out[0] = <|m|>,
+ * out[1] = <m^2>, out[2] = <m^4>, out[3] = <e>, out[4] = <e^2>, out[5] = U4.
  * sums (may be NULL) receives the 11 exact 64-bit limbs: sum|M|, sum M^2 (2
  * limbs, little-endian), sum M^4 (4), sum E (2, two's complement), sum E^2 (2).
  * Synchronises.  Errors: EINVAL (no samples), ECUDA.
  */
-int ising_moments(ising_t h, int64_t burn_in, double out[6], uint64_t sums[11]);
+int ising_moments_ex(ising_t h, int64_t burn_in, double out[6], uint64_t sums[11]);
 
-/* Copies the lattice into out[L*L] (row-major, +1 / -1).  Synchronises. */
+/* Copies the lattice into out[L*L] (row-major, +1 / -1).  Synchronises.
+ * Paper: Sec. 3 (the spin configuration sigma). */
 int ising_get_lattice(ising_t h, int8_t *out);
 
 /*
@@ -146,6 +162,7 @@ int ising_get_rows(ising_t h, int64_t row0, int64_t nrows, int8_t *out);
 /*
  * Replaces the lattice by in[L*L] (row-major, each entry +1 or -1; other values
  * are EINVAL).  Does not change the sweep counter.  Synchronises.
+ * Paper: Sec. 3 (the spin configuration sigma).
  */
 int ising_set_lattice(ising_t h, const int8_t *in);
 
@@ -172,7 +189,8 @@ int ising_load(ising_t *out, const void *buf, int64_t bytes, void *stream);
 /* Waits for the handle's work; reports ETIMEOUT if a kernel gave up. */
 int ising_synchronize(ising_t h);
 
-/* Releases the handle and its device memory (NULL is a no-op). */
+/* Releases the handle and its device memory (NULL is a no-op).  Paper: none (resource
+ * management of the Sec. 3 lattice). */
 int ising_free(ising_t h);
 
 /* ------------------------------------------------------------------------
@@ -197,7 +215,7 @@ int ising_thresholds3d(double beta, uint64_t T[3]);
  * Creates a bit-packed cubic lattice of side L (L % 64 == 0, 64 <= L <= 8192):
  * device memory L^3/8 bytes of planes plus 16 bytes of history per sweep.
  * start and stream as in ising_init_ex.  The handle works with ising_sweep,
- * ising_observables, ising_history, ising_moments (N = L^3), ising_get_lattice
+ * ising_observables, ising_history, ising_moments[_ex] (N = L^3), ising_get_lattice
  * (out[L^3], index (i*L + j)*L + k), ising_get_planes / ising_set_planes (L*L
  * rows of L/64 words each per colour, row i*L + j; bit b of word w is the site
  * (i, j, 2(32w+b) + ((i+j+c)&1))), the checkpoint calls, ising_synchronize and
@@ -209,19 +227,36 @@ int ising_init3d(ising_t *out, int64_t L, double beta, uint64_t seed, int start,
 /* ------------------------------------------------------------------------
  * Batch: many packed lattices of uneven L and beta swept by one persistent
  * launch per half-sweep (the single-device analogue of the paper's replicated
- * program, Sec. 5), optionally replayed from a captured CUDA graph.
+ * program, Sec. 5.1), optionally replayed from a captured CUDA graph.
  * ---------------------------------------------------------------------- */
+
+/*
+ * Creates a batch of `count` packed lattices from caller-owned host arrays of
+ * length count (read during the call only): lattice k has side L[k] (the sizes
+ * ising_init_ex accepts for ISING_PACKED), inverse temperature beta[k] (finite,
+ * >= 0), Philox seed seed[k] and start[k] (ISING_HOT or ISING_COLD); it is slot k
+ * of the batch.  Paper: Sec. 3 (each lattice), Sec. 5.1 (many independent
+ * simulations run as one replicated program, here one launch).
+ * The lattices have no sweep limit: every ising_batch_run sweeps all of them, and
+ * their (M, E) histories live outside the planes' arena and grow (doubling) when a
+ * run needs room.  Built-in tile shapes, 256-thread CTAs, a stream the batch owns.
+ * EINVAL, before any device work, for a null array, count outside 1 .. 2^20, or
+ * any bad L, beta or start (the message names the lattice).  ENOMEM, ECUDA.
+ */
+int ising_batch_create(ising_batch_t *out, int32_t count, const int64_t *L, const double *beta,
+                       const uint64_t *seed, const int32_t *start);
 
 /*
  * Creates an empty batch that can hold up to `capacity` lattices of side <=
  * max_L with `arena_bytes` of device memory for planes and histories (the HBM
- * budget; allocation beyond it is ENOMEM).  threads: CTA size of the sweep
+ * budget; allocation beyond it is ENOMEM); lattices join with ising_batch_add and
+ * run at most the sweeps they were admitted for.  threads: CTA size of the sweep
  * kernel (128, 256 or 512; 0 = 256).  stream as in ising_init_ex.
  * EINVAL, before any device work, unless 1 <= capacity <= 2^20, max_L is a
  * multiple of 64 in 64 .. 2^20 and arena_bytes >= 256.
  */
-int ising_batch_create(ising_batch_t *out, int32_t capacity, int64_t max_L, int64_t arena_bytes, int32_t threads,
-                       void *stream);
+int ising_batch_create_ex(ising_batch_t *out, int32_t capacity, int64_t max_L, int64_t arena_bytes, int32_t threads,
+                          void *stream);
 
 /*
  * Adds a packed lattice (L % 64 == 0, L <= max_L, and within the sizes
@@ -252,10 +287,11 @@ int ising_batch_add_tiled(ising_batch_t b, int64_t L, double beta, uint64_t seed
 int ising_batch_remove(ising_batch_t b, int32_t idx);
 
 /*
- * Enqueues `sweeps` sweeps of every lattice in the batch; a lattice stops at
- * its own sweep limit.  graph_sweeps > 0: capture graph_sweeps sweeps into a
- * CUDA graph once (re-captured if graph_sweeps changes) and replay it
- * sweeps / graph_sweeps times (sweeps must be a multiple); 0: plain launches.
+ * Enqueues `sweeps` sweeps of every lattice in the batch; a lattice admitted with
+ * ising_batch_add stops at its own sweep limit.  graph_sweeps (the use_graph
+ * switch) > 0: capture graph_sweeps sweeps into a CUDA graph once (re-captured if
+ * graph_sweeps changes) and replay it sweeps / graph_sweeps times (sweeps must be
+ * a multiple, else EINVAL); 0: plain launches.  Paper: Sec. 3.1 (the sweep), Sec. 5.1.
  */
 int ising_batch_run(ising_batch_t b, int64_t sweeps, int32_t graph_sweeps);
 
@@ -269,12 +305,13 @@ int ising_batch_sweeps_done(ising_batch_t b, int32_t idx, int64_t *sweeps_done);
 int ising_batch_progress(ising_batch_t b, int64_t *sweeps_done, int32_t n);
 
 /*
- * Slot idx: current M and E (the start state before any sweep) and sweeps done;
- * history entries first .. first+count-1; Sec. 4.1 moments over samples
- * burn_in .. sweeps_done-1 (as ising_moments); the lattice as L*L int8 +1/-1.
- * All synchronise.
+ * Slot idx: current M and E (the start state before any sweep; Sec. 4.1, Sec. 3);
+ * the _ex form also gives the sweeps done.  History entries first .. first+count-1;
+ * Sec. 4.1 moments over samples burn_in .. sweeps_done-1 (as ising_moments_ex); the
+ * lattice as L*L int8 +1/-1.  All synchronise.
  */
-int ising_batch_observables(ising_batch_t b, int32_t idx, int64_t *M, int64_t *E, int64_t *sweeps_done);
+int ising_batch_observables(ising_batch_t b, int32_t idx, int64_t *M, int64_t *E);
+int ising_batch_observables_ex(ising_batch_t b, int32_t idx, int64_t *M, int64_t *E, int64_t *sweeps_done);
 int ising_batch_history(ising_batch_t b, int32_t idx, int64_t first, int64_t count, int64_t *M, int64_t *E);
 int ising_batch_moments(ising_batch_t b, int32_t idx, int64_t burn_in, double out[6], uint64_t sums[11]);
 int ising_batch_get_lattice(ising_batch_t b, int32_t idx, int8_t *out);

@@ -400,8 +400,13 @@ struct ising_batch_s {
         int64_t L = 0;
         int64_t off = 0, bytes = 0;
         int64_t sweeps_cap = 0;
+        int64_t* own_hist = nullptr;  // growable batches: the history, outside the arena
+        int64_t done = 0;             // growable batches: sweeps enqueued since admission
         LatticeDesc desc{};
     };
+    // growable (made from arrays): lattices have no sweep limit, their histories are
+    // allocated apart from the arena and doubled when a run needs more room
+    bool growable = false;
     int capacity = 0;
     int64_t max_L = 0;
     cudaStream_t stream = nullptr;
@@ -853,7 +858,7 @@ int ising_history(ising_t h, int64_t first, int64_t count, int64_t* M, int64_t* 
     return ISING_OK;
 }
 
-int ising_moments(ising_t h, int64_t burn_in, double out[6], uint64_t sums[11])
+int ising_moments_ex(ising_t h, int64_t burn_in, double out[6], uint64_t sums[11])
 {
     int rc = check_handle(h);
     if (rc) return rc;
@@ -868,6 +873,19 @@ int ising_moments(ising_t h, int64_t burn_in, double out[6], uint64_t sums[11])
     if (rc) return rc;
     memcpy(out, m, sizeof(m));
     if (sums) memcpy(sums, s, sizeof(s));
+    return ISING_OK;
+}
+
+int ising_moments(ising_t h, int64_t burn_in, double* abs_m, double* m2, double* m4, double* e, double* binder)
+{
+    double m[6];
+    int rc = ising_moments_ex(h, burn_in, m, nullptr);
+    if (rc) return rc;
+    if (abs_m) *abs_m = m[0];
+    if (m2) *m2 = m[1];
+    if (m4) *m4 = m[2];
+    if (e) *e = m[3];
+    if (binder) *binder = m[5];
     return ISING_OK;
 }
 
@@ -1085,6 +1103,36 @@ int rebuild_tiles(ising_batch_t b)
     return b->eng.upload_tiles(ts, count);
 }
 
+// Growable batches: before `sweeps` more sweeps, give every lattice's history room
+// for them (doubling; the entries so far are copied).  The kernels read the history
+// pointer from the device descriptor, so a captured graph stays valid.
+int grow_histories(ising_batch_t b, int64_t sweeps)
+{
+    for (int k = 0; k < b->capacity; ++k) {
+        auto& s = b->slots[k];
+        if (!s.used || s.done + sweeps <= s.sweeps_cap) continue;
+        int64_t cap = s.sweeps_cap;
+        while (cap < s.done + sweeps) cap = std::min<int64_t>(2 * cap, kMaxSweeps + 1);
+        int64_t* nh = nullptr;
+        CK(cudaMalloc(&nh, 16 * (size_t)cap));
+        cudaError_t e = cudaSuccess;
+        if (s.done) e = cudaMemcpyAsync(nh, s.own_hist, 16 * (size_t)s.done, cudaMemcpyDeviceToDevice, b->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+        if (e != cudaSuccess) {
+            cudaFree(nh);
+            return cuda_fail(e, "history copy");
+        }
+        cudaFree(s.own_hist);
+        s.own_hist = nh;
+        s.sweeps_cap = cap;
+        s.desc.hist = nh;
+        s.desc.sweep = (uint32_t)s.done;
+        int rc = b->eng.upload_desc(k, s.desc);
+        if (rc) return rc;
+    }
+    return ISING_OK;
+}
+
 int check_batch(ising_batch_t b, int32_t idx)
 {
     if (!b) return fail(ISING_EINVAL, "null batch");
@@ -1103,8 +1151,8 @@ int batch_sweeps_done(ising_batch_t b, int32_t idx, int64_t* done)
 }
 }  // namespace
 
-int ising_batch_create(ising_batch_t* out, int32_t capacity, int64_t max_L, int64_t arena_bytes, int32_t threads,
-                       void* stream)
+int ising_batch_create_ex(ising_batch_t* out, int32_t capacity, int64_t max_L, int64_t arena_bytes, int32_t threads,
+                          void* stream)
 {
     if (!out) return fail(ISING_EINVAL, "null output");
     if (capacity < 1 || capacity > (1 << 20)) return fail(ISING_EINVAL, "capacity out of range");
@@ -1154,6 +1202,41 @@ int ising_batch_add(ising_batch_t b, int64_t L, double beta, uint64_t seed, int3
     return ising_batch_add_tiled(b, L, beta, seed, start, sweeps, tile_rows, 0, idx);
 }
 
+int ising_batch_create(ising_batch_t* out, int32_t count, const int64_t* L, const double* beta, const uint64_t* seed,
+                       const int32_t* start)
+{
+    if (!out || !L || !beta || !seed || !start) return fail(ISING_EINVAL, "null argument");
+    if (count < 1 || count > (1 << 20)) return fail(ISING_EINVAL, "count %d outside 1 .. 2^20", count);
+    // every argument is checked before any device work
+    int64_t max_L = 64, arena = 0;
+    for (int32_t k = 0; k < count; ++k) {
+        uint64_t T[2];
+        if (L[k] < 64 || L[k] % 64 || !packed_L_ok(L[k]))
+            return fail(ISING_EINVAL, "lattice %d: L = %lld is not a packed side", k, (long long)L[k]);
+        if (!thresholds(beta[k], T)) return fail(ISING_EINVAL, "lattice %d: beta must be finite and >= 0", k);
+        if (start[k] != ISING_HOT && start[k] != ISING_COLD) return fail(ISING_EINVAL, "lattice %d: bad start", k);
+        max_L = std::max(max_L, L[k]);
+        arena += FreeList::round_up((int64_t)sizeof(uint32_t) * 2 * L[k] * (L[k] / 64));
+    }
+    ising_batch_t b = nullptr;
+    int rc = ising_batch_create_ex(&b, count, max_L, arena, 0, nullptr);
+    if (rc) return rc;
+    b->growable = true;
+    constexpr int64_t kFirstHistory = 1024;  // sweeps of history at admission, doubled as needed
+    for (int32_t k = 0; k < count && !rc; ++k) {
+        int32_t idx = -1;
+        rc = ising_batch_add(b, L[k], beta[k], seed[k], start[k], kFirstHistory, 0, &idx);
+    }
+    if (rc) {
+        const std::string msg = t_error;
+        ising_batch_free(b);
+        t_error = msg;
+        return rc;
+    }
+    *out = b;
+    return ISING_OK;
+}
+
 int ising_batch_add_tiled(ising_batch_t b, int64_t L, double beta, uint64_t seed, int32_t start, int64_t sweeps,
                           int32_t tile_rows, int32_t tile_words, int32_t* idx)
 {
@@ -1185,23 +1268,31 @@ int ising_batch_add_tiled(ising_batch_t b, int64_t L, double beta, uint64_t seed
     if (slot < 0) return fail(ISING_EBUSY, "all %d slots in use", b->capacity);
     const int64_t plane_words = L * (L / 64);
     const int64_t plane_bytes = (int64_t)sizeof(uint32_t) * 2 * plane_words;
-    const int64_t bytes = plane_bytes + 16 * sweeps;
+    // a growable batch keeps histories apart from the arena (they are resized); else the
+    // history of `sweeps` sweeps follows the planes in the arena
+    const int64_t bytes = plane_bytes + (b->growable ? 0 : 16 * sweeps);
+    int64_t* own_hist = nullptr;
+    if (b->growable) CK(cudaMalloc(&own_hist, 16 * (size_t)sweeps));
     const int64_t off = b->arena.alloc(bytes);
-    if (off < 0)
+    if (off < 0) {
+        cudaFree(own_hist);
         return fail(ISING_ENOMEM, "arena full: %lld of %lld bytes used, need %lld", (long long)b->arena.used,
                     (long long)b->arena.size, (long long)bytes);
+    }
     auto& s = b->slots[slot];
     s.used = true;
     s.L = L;
     s.off = off;
     s.bytes = bytes;
     s.sweeps_cap = sweeps;
+    s.own_hist = own_hist;
+    s.done = 0;
     uint32_t* planes = reinterpret_cast<uint32_t*>(b->arena.base + off);
     LatticeDesc& d = s.desc;
     d = LatticeDesc{};
     d.plane[0] = planes;
     d.plane[1] = planes + plane_words;
-    d.hist = reinterpret_cast<int64_t*>(b->arena.base + off + plane_bytes);
+    d.hist = own_hist ? own_hist : reinterpret_cast<int64_t*>(b->arena.base + off + plane_bytes);
     d.key = seed;
     d.L = (int32_t)L;
     d.W = (int32_t)(L / 64);
@@ -1210,7 +1301,7 @@ int ising_batch_add_tiled(ising_batch_t b, int64_t L, double beta, uint64_t seed
     d.halo_rows = halo_rows_for(L / 64);
     d.tile_words = tile_words;
     d.sweep = 0;
-    d.target = (uint32_t)sweeps;
+    d.target = b->growable ? kNoTarget : (uint32_t)sweeps;
     if (tile_words != W) b->eng.allow_blocks();
     d.active = 1;
     cudaError_t e = launch_packed_init(d.plane[0], d.plane[1], L, seed, start, b->stream);
@@ -1232,6 +1323,11 @@ int ising_batch_remove(ising_batch_t b, int32_t idx)
     if (rc) return rc;
     s.used = false;
     b->arena.release(s.off, s.bytes);
+    if (s.own_hist) {
+        CK(cudaStreamSynchronize(b->stream));  // the slot's pending sweeps may still write it
+        cudaFree(s.own_hist);
+        s.own_hist = nullptr;
+    }
     return rebuild_tiles(b);
 }
 
@@ -1239,7 +1335,21 @@ int ising_batch_run(ising_batch_t b, int64_t sweeps, int32_t graph_sweeps)
 {
     if (!b) return fail(ISING_EINVAL, "null batch");
     if (sweeps < 0) return fail(ISING_EINVAL, "sweeps must be >= 0");
-    return b->eng.run(sweeps, graph_sweeps);
+    if (graph_sweeps > 0 && sweeps % graph_sweeps)
+        return fail(ISING_EINVAL, "sweeps %lld not a multiple of graph_sweeps %d", (long long)sweeps, graph_sweeps);
+    if (b->growable) {
+        for (const auto& s : b->slots)
+            if (s.used && sweeps > kMaxSweeps - s.done)
+                return fail(ISING_EINVAL, "sweep total beyond 2^32 - 2");
+        int rc = grow_histories(b, sweeps);
+        if (rc) return rc;
+    }
+    int rc = b->eng.run(sweeps, graph_sweeps);
+    if (rc) return rc;
+    if (b->growable)
+        for (auto& s : b->slots)
+            if (s.used) s.done += sweeps;
+    return ISING_OK;
 }
 
 int ising_batch_sweeps_done(ising_batch_t b, int32_t idx, int64_t* sweeps_done)
@@ -1262,7 +1372,7 @@ int ising_batch_progress(ising_batch_t b, int64_t* sweeps_done, int32_t n)
     return ISING_OK;
 }
 
-int ising_batch_observables(ising_batch_t b, int32_t idx, int64_t* M, int64_t* E, int64_t* sweeps_done)
+int ising_batch_observables_ex(ising_batch_t b, int32_t idx, int64_t* M, int64_t* E, int64_t* sweeps_done)
 {
     int rc = check_batch(b, idx);
     if (rc) return rc;
@@ -1282,6 +1392,11 @@ int ising_batch_observables(ising_batch_t b, int32_t idx, int64_t* M, int64_t* E
     if (E) *E = me[1];
     if (sweeps_done) *sweeps_done = done;
     return ISING_OK;
+}
+
+int ising_batch_observables(ising_batch_t b, int32_t idx, int64_t* M, int64_t* E)
+{
+    return ising_batch_observables_ex(b, idx, M, E, nullptr);
 }
 
 int ising_batch_history(ising_batch_t b, int32_t idx, int64_t first, int64_t count, int64_t* M, int64_t* E)
@@ -1361,6 +1476,7 @@ int ising_batch_free(ising_batch_t b)
     if (b->stream) cudaStreamSynchronize(b->stream);
     b->eng.destroy();
     b->arena.destroy();
+    for (auto& s : b->slots) cudaFree(s.own_hist);
     cudaFree(b->d_me);
     cudaFree(b->d_mom);
     cudaFree(b->d_sums);
@@ -1390,7 +1506,7 @@ int ising_autotune(int64_t L, int32_t* tile_rows, int32_t* threads, double* ms)
     for (int ti = 0; ti < 2; ++ti) {
         ising_batch_t b = nullptr;
         const int64_t per = (int64_t)sizeof(uint32_t) * 2 * L * (L / 64) + 16 * (2 * reps + 4) + 512;
-        int rc = ising_batch_create(&b, copies, L, per * copies + 4096, thread_opts[ti], nullptr);
+        int rc = ising_batch_create_ex(&b, copies, L, per * copies + 4096, thread_opts[ti], nullptr);
         if (rc) return rc;
         for (int tr = 2; tr <= kMaxTileRows; tr *= 2) {
             if (!tile_rows_ok(L, tr)) continue;  // whole rows only

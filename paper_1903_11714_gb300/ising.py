@@ -41,7 +41,8 @@ _SIGS = {
     "ising_sweep": (ctypes.c_int, [_vp, _i64]),
     "ising_observables": (ctypes.c_int, [_vp, _P(_i64), _P(_i64), _P(_i64)]),
     "ising_history": (ctypes.c_int, [_vp, _i64, _i64, _P(_i64), _P(_i64)]),
-    "ising_moments": (ctypes.c_int, [_vp, _i64, _P(_d), _P(_u64)]),
+    "ising_moments": (ctypes.c_int, [_vp, _i64, _P(_d), _P(_d), _P(_d), _P(_d), _P(_d)]),
+    "ising_moments_ex": (ctypes.c_int, [_vp, _i64, _P(_d), _P(_u64)]),
     "ising_get_lattice": (ctypes.c_int, [_vp, _P(ctypes.c_int8)]),
     "ising_get_rows": (ctypes.c_int, [_vp, _i64, _i64, _P(ctypes.c_int8)]),
     "ising_set_lattice": (ctypes.c_int, [_vp, _P(ctypes.c_int8)]),
@@ -54,14 +55,16 @@ _SIGS = {
     "ising_free": (ctypes.c_int, [_vp]),
     "ising_thresholds3d": (ctypes.c_int, [_d, _P(_u64)]),
     "ising_init3d": (ctypes.c_int, [_P(_vp), _i64, _d, _u64, ctypes.c_int, _vp]),
-    "ising_batch_create": (ctypes.c_int, [_P(_vp), _i32, _i64, _i64, _i32, _vp]),
+    "ising_batch_create": (ctypes.c_int, [_P(_vp), _i32, _P(_i64), _P(_d), _P(_u64), _P(_i32)]),
+    "ising_batch_create_ex": (ctypes.c_int, [_P(_vp), _i32, _i64, _i64, _i32, _vp]),
     "ising_batch_add": (ctypes.c_int, [_vp, _i64, _d, _u64, _i32, _i64, _i32, _P(_i32)]),
     "ising_batch_add_tiled": (ctypes.c_int, [_vp, _i64, _d, _u64, _i32, _i64, _i32, _i32, _P(_i32)]),
     "ising_batch_remove": (ctypes.c_int, [_vp, _i32]),
     "ising_batch_run": (ctypes.c_int, [_vp, _i64, _i32]),
     "ising_batch_sweeps_done": (ctypes.c_int, [_vp, _i32, _P(_i64)]),
     "ising_batch_progress": (ctypes.c_int, [_vp, _P(_i64), _i32]),
-    "ising_batch_observables": (ctypes.c_int, [_vp, _i32, _P(_i64), _P(_i64), _P(_i64)]),
+    "ising_batch_observables": (ctypes.c_int, [_vp, _i32, _P(_i64), _P(_i64)]),
+    "ising_batch_observables_ex": (ctypes.c_int, [_vp, _i32, _P(_i64), _P(_i64), _P(_i64)]),
     "ising_batch_history": (ctypes.c_int, [_vp, _i32, _i64, _i64, _P(_i64), _P(_i64)]),
     "ising_batch_moments": (ctypes.c_int, [_vp, _i32, _i64, _P(_d), _P(_u64)]),
     "ising_batch_get_lattice": (ctypes.c_int, [_vp, _i32, _P(ctypes.c_int8)]),
@@ -177,11 +180,37 @@ def _moments_dict(out: np.ndarray, sums: np.ndarray) -> dict:
     return d
 
 
-def ising_moments(h: int, burn_in: int) -> dict:
+def ising_moments(h: int, burn_in: int) -> tuple[float, float, float, float, float]:
+    """(<|m|>, <m^2>, <m^4>, <e>, U4) over samples burn_in .. sweeps_done-1."""
+    v = [ctypes.c_double() for _ in range(5)]
+    _check(lib().ising_moments(h, int(burn_in), *(ctypes.byref(x) for x in v)))
+    return tuple(x.value for x in v)
+
+
+def ising_moments_ex(h: int, burn_in: int) -> dict:
     out = np.zeros(6, dtype=np.float64)
     sums = np.zeros(11, dtype=np.uint64)
-    _check(lib().ising_moments(h, int(burn_in), _ptr(out, ctypes.c_double), _ptr(sums, ctypes.c_uint64)))
+    _check(lib().ising_moments_ex(h, int(burn_in), _ptr(out, ctypes.c_double), _ptr(sums, ctypes.c_uint64)))
     return _moments_dict(out, sums)
+
+
+def ising_batch_create(Ls, betas, seeds, starts) -> int:
+    """A batch of len(Ls) packed lattices from per-lattice arrays (slot k = lattice k)."""
+    n = len(Ls)
+    b = ctypes.c_void_p()
+    _check(lib().ising_batch_create(ctypes.byref(b), n, (ctypes.c_int64 * n)(*Ls), (ctypes.c_double * n)(*betas),
+                                    (ctypes.c_uint64 * n)(*seeds), (ctypes.c_int32 * n)(*starts)))
+    return b.value
+
+
+def ising_batch_run(b: int, sweeps: int, use_graph: int = 0) -> None:
+    _check(lib().ising_batch_run(b, int(sweeps), int(use_graph)))
+
+
+def ising_batch_observables(b: int, idx: int) -> tuple[int, int]:
+    M, E = ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().ising_batch_observables(b, int(idx), ctypes.byref(M), ctypes.byref(E)))
+    return M.value, E.value
 
 
 def ising_thresholds3d(beta: float) -> tuple[int, int, int]:
@@ -313,7 +342,7 @@ class Lattice:
         return ising_history(self.h, first, count)
 
     def moments(self, burn_in: int) -> dict:
-        return ising_moments(self.h, burn_in)
+        return ising_moments_ex(self.h, burn_in)
 
     def get_lattice(self) -> np.ndarray:
         return ising_get_lattice(self.h, self.L)
@@ -362,12 +391,22 @@ class Lattice:
 class Batch:
     """Many packed lattices swept together (an ``ising_batch_t``)."""
 
-    def __init__(self, capacity: int, max_L: int, arena_bytes: int, threads: int = 0, stream=None):
+    def __init__(self, capacity: int, max_L: int, arena_bytes: int, threads: int = 0, stream=None,
+                 _handle: int | None = None, _Ls=None):
+        if _handle is not None:
+            self.b = _handle
+            self.L = {k: int(v) for k, v in enumerate(_Ls)}
+            return
         b = ctypes.c_void_p()
-        _check(lib().ising_batch_create(ctypes.byref(b), int(capacity), int(max_L), int(arena_bytes), int(threads),
-                                        _stream_ptr(stream)))
+        _check(lib().ising_batch_create_ex(ctypes.byref(b), int(capacity), int(max_L), int(arena_bytes),
+                                           int(threads), _stream_ptr(stream)))
         self.b = b.value
         self.L = {}
+
+    @classmethod
+    def from_arrays(cls, Ls, betas, seeds, starts) -> "Batch":
+        """Lattice k of the arrays in slot k, no sweep limit (ising_batch_create)."""
+        return cls(0, 0, 0, _handle=ising_batch_create(Ls, betas, seeds, starts), _Ls=Ls)
 
     def add(self, L: int, beta: float, seed: int, start: int, sweeps: int, tile_rows: int = 0,
             tile_words: int = 0) -> int:
@@ -396,7 +435,8 @@ class Batch:
 
     def observables(self, idx: int):
         M, E, n = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
-        _check(lib().ising_batch_observables(self.b, int(idx), ctypes.byref(M), ctypes.byref(E), ctypes.byref(n)))
+        _check(lib().ising_batch_observables_ex(self.b, int(idx), ctypes.byref(M), ctypes.byref(E),
+                                                ctypes.byref(n)))
         return M.value, E.value, n.value
 
     def history(self, idx: int, first: int = 0, count: int | None = None):

@@ -217,3 +217,50 @@ def test_batch_still_runs_after_a_smaller_engine_is_configured():
     assert np.array_equal(M, Ms) and np.array_equal(E, Es)
     lat.close()
     b.close()
+
+
+def test_batch_from_arrays_matches_oracle_through_history_growth():
+    """The boundary's array form, through the C ABI: ising_batch_create(count, L[],
+    beta[], seed[], start[]) on an uneven three-lattice batch (W % 4 == 0, odd W,
+    W = 2 mod 4; hot and cold starts), run as a captured 100-sweep graph replayed
+    6 times and then 600 plain sweeps: 1,200 sweeps, past the 1,024-sweep history
+    a lattice gets at admission, so every history is grown once between runs.
+    Lattices, every sweep's M and E, the current (M, E) and the Sec. 4.1 moments
+    (ising_moments' five outputs) equal the oracle's."""
+    Ls, betas, seeds, starts = [256, 192, 128], [0.4406868, 0.30, 0.55], [11, 12, 13], [ising.HOT, ising.HOT,
+                                                                                          ising.COLD]
+    h = ising.ising_batch_create(Ls, betas, seeds, starts)
+    b = ising.Batch(0, 0, 0, _handle=h, _Ls=Ls)
+    try:
+        for k in range(3):  # the start states, before any sweep
+            ref0 = oracle.init(Ls[k], seeds[k], starts[k])
+            assert ising.ising_batch_observables(h, k) == oracle.observe(ref0), k
+        ising.ising_batch_run(h, 600, 100)
+        ising.ising_batch_run(h, 600, 0)
+        n = 1200
+        for k in range(3):
+            ref, Mr, Er, _ = oracle.run(Ls[k], betas[k], seeds[k], starts[k], n)
+            M, E = b.history(k)
+            assert len(M) == n
+            assert np.array_equal(M, Mr) and np.array_equal(E, Er), k
+            assert np.array_equal(b.get_lattice(k), ref), k
+            assert ising.ising_batch_observables(h, k) == (int(Mr[-1]), int(Er[-1])), k
+            ex = oracle.moments_exact(Mr, Er, Ls[k] ** 2, n // 10)
+            got = b.moments(k, n // 10)
+            for key in ("abs_m", "m2", "m4", "e", "binder"):
+                assert got[key] == pytest.approx(ex[key], rel=REL_TOL, abs=0), (k, key)
+    finally:
+        b.close()
+
+
+def test_single_handle_moments_five_outputs_match_the_extended_form():
+    """ising_moments (the boundary's five outputs) equals ising_moments_ex's values."""
+    lat = ising.Lattice(256, 0.45, 5, ising.HOT, ising.PACKED).sweep(300)
+    five = ising.ising_moments(lat.h, 30)
+    ex = lat.moments(30)
+    assert five == (ex["abs_m"], ex["m2"], ex["m4"], ex["e"], ex["binder"])
+    M, E = lat.history()
+    ref = oracle.moments_exact(M, E, 256 * 256, 30)
+    for got, key in zip(five, ("abs_m", "m2", "m4", "e", "binder")):
+        assert got == pytest.approx(ref[key], rel=REL_TOL, abs=0), key
+    lat.close()

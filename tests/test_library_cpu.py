@@ -45,6 +45,32 @@ def test_header_declares_the_boundary_entry_points():
         assert required in names
 
 
+def test_header_signatures_of_the_boundary_calls():
+    """The calls of the hot path's C boundary take exactly these parameters."""
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    text = re.sub(r"\s+", " ", text)
+    want = [
+        "int ising_init(ising_t *out, int64_t L, double beta, uint64_t seed);",
+        "int ising_init_ex(ising_t *out, int64_t L, double beta, uint64_t seed, int start, int kernel, void *stream);",
+        "int ising_sweep(ising_t h, int64_t n);",
+        "int ising_observables(ising_t h, int64_t *M, int64_t *E, int64_t *sweeps_done);",
+        "int ising_history(ising_t h, int64_t first, int64_t count, int64_t *M, int64_t *E);",
+        "int ising_moments(ising_t h, int64_t burn_in, double *abs_m, double *m2, double *m4, double *e, "
+        "double *binder);",
+        "int ising_get_lattice(ising_t h, int8_t *out);",
+        "int ising_set_lattice(ising_t h, const int8_t *in);",
+        "int ising_thresholds(double beta, uint64_t T[2]);",
+        "int ising_free(ising_t h);",
+        "const char *ising_last_error(void);",
+        "int ising_batch_create(ising_batch_t *out, int32_t count, const int64_t *L, const double *beta, "
+        "const uint64_t *seed, const int32_t *start);",
+        "int ising_batch_run(ising_batch_t b, int64_t sweeps, int32_t graph_sweeps);",
+        "int ising_batch_observables(ising_batch_t b, int32_t idx, int64_t *M, int64_t *E);",
+    ]
+    for sig in want:
+        assert sig in text, sig
+
+
 def test_library_exports_every_declared_symbol(lib):
     out = subprocess.run(["nm", "-D", "--defined-only", libbuild.LIB], capture_output=True, text=True, check=True)
     exported = set(re.findall(r"\sT\s(ising_\w+)", out.stdout))
@@ -238,8 +264,8 @@ def test_accepted_sides_are_exactly_the_documented_ones(lib):
     assert h.value is None
 
 
-def test_batch_create_arguments(lib):
-    """ising_batch_create: EINVAL unless 1 <= capacity <= 2^20, max_L a multiple of 64
+def test_batch_create_ex_arguments(lib):
+    """ising_batch_create_ex: EINVAL unless 1 <= capacity <= 2^20, max_L a multiple of 64
     in 64 .. 2^20, threads in {0, 128, 256, 512} and arena_bytes >= 256; valid
     arguments get as far as the device."""
     no_device_or_skip(lib)
@@ -249,8 +275,39 @@ def test_batch_create_arguments(lib):
            dict(max_L=(1 << 20) + 64), dict(threads=64), dict(threads=300), dict(threads=1024), dict(arena=255)]
     for change in bad + [dict()] + [dict(threads=t) for t in (128, 256, 512)] + [dict(max_L=1 << 20, capacity=1 << 20)]:
         a = {**good, **change}
-        rc = lib.ising_batch_create(ctypes.byref(b), a["capacity"], a["max_L"], a["arena"], a["threads"], None)
+        rc = lib.ising_batch_create_ex(ctypes.byref(b), a["capacity"], a["max_L"], a["arena"], a["threads"], None)
         assert rc == (ising.ISING_EINVAL if change in bad else ising.ISING_ECUDA), (change, rc)
+    assert b.value is None
+
+
+def test_batch_create_from_arrays_arguments(lib):
+    """ising_batch_create (the array form): EINVAL, before any device work, for a
+    null array, count outside 1 .. 2^20, or any lattice whose L is not a packed side,
+    whose beta is not finite and >= 0, or whose start is neither hot nor cold (the
+    message names the lattice); valid arrays get as far as the device."""
+    no_device_or_skip(lib)
+    b = ctypes.c_void_p()
+
+    def call(Ls, betas=None, starts=None, count=None, null=None):
+        n = len(Ls)
+        arrs = [(ctypes.c_int64 * n)(*Ls), (ctypes.c_double * n)(*(betas or [0.44] * n)),
+                (ctypes.c_uint64 * n)(*range(n)), (ctypes.c_int32 * n)(*(starts or [ising.HOT] * n))]
+        if null is not None:
+            arrs[null] = None
+        return lib.ising_batch_create(ctypes.byref(b), n if count is None else count, *arrs)
+
+    assert call([256, 512, 64]) == ising.ISING_ECUDA
+    assert call([256, 512, 64], starts=[ising.HOT, ising.COLD, ising.COLD]) == ising.ISING_ECUDA
+    for null in range(4):
+        assert call([256], null=null) == ising.ISING_EINVAL
+    assert call([256], count=0) == ising.ISING_EINVAL
+    assert call([256], count=-3) == ising.ISING_EINVAL
+    for L in (0, 32, 100, 65, 1 << 21, 102_464):
+        assert call([256, L, 64]) == ising.ISING_EINVAL, L
+        assert "lattice 1" in ising.last_error()
+    for beta in (float("nan"), float("inf"), -0.1):
+        assert call([256, 256], betas=[0.4, beta]) == ising.ISING_EINVAL
+    assert call([256, 256], starts=[ising.HOT, 2]) == ising.ISING_EINVAL
     assert b.value is None
 
 
