@@ -46,7 +46,8 @@ ISSUE_SLOTS_PER_CLK_SM = 128.0
 ALU_OPS_PER_CLK_SM = 64.0
 N_SMS = 152
 KERNEL_SOURCES = {
-    "packed_half_sweep": ("sweep_packed.cu", "word_update.cuh", "philox.cuh", "ising_internal.cuh"),
+    "packed_half_sweep": ("sweep_packed_kernel.cuh", "word_update.cuh", "philox.cuh", "ising_device.cuh",
+                          "jit.cu"),
     "cubic_half_sweep": ("sweep3d.cu", "sweep3d.cuh", "word_update.cuh", "philox.cuh"),
 }
 # algorithmic bytes per site per sweep (packed): each half-sweep reads the target
@@ -173,33 +174,59 @@ def committed_counters(kernel: str):
         d = json.load(f)
     sites = d["sites_per_launch"]
     alu = d.get("alu_warp_inst_per_launch")
+    pipes = {name: d[f"{name}_pipe_cycles_per_launch"] / sites for name in ("alu", "fmaheavy")
+             if f"{name}_pipe_cycles_per_launch" in d}
     return {"current": d.get("kernel_source_hash") == kernel_source_hash(kernel),
             "inst_slots_per_site": 32.0 * d["warp_inst_per_launch"] / sites,
             "alu_ops_per_site": None if alu is None else 32.0 * alu / sites,
+            "pipe_cycles_per_site": pipes or None,
             "dram_bytes_per_site": (d["dram_bytes_read_per_launch"] + d["dram_bytes_write_per_launch"]) / sites,
             "capture": d.get("command")}
 
 
+PIPE_NAMES = {"alu": "ALU pipe (logic, shifts, compares)",
+              "fmaheavy": "FMA-heavy pipe (integer multiplies: the Philox products)"}
+
+
 def kernel_roofline(kernel: str, sites_per_launch: float, t_launch_s: float, sm_max: float, peaks: dict) -> dict:
-    """Roofline of one half-sweep launch.  The binding unit is the ALU pipe (16 lanes x 4
-    schedulers per SM; the busiest pipe in the committed ncu counters), so `achieved` is
-    the launch's ALU-pipe thread operations (ncu sm__inst_executed_pipe_alu.sum x 32,
-    committed with a hash of the kernel's sources) per second of CUDA-event time, against
-    64 lanes/clk/SM x SMs x the maximum SM clock.  The instruction-issue view (every
-    instruction takes one of 128 thread slots/clk/SM) and the HBM view ride along."""
+    """Roofline of one half-sweep launch.  The sweep is integer work on two pipes of 16
+    lanes per scheduler (4 per SM): the ALU pipe (the Philox XORs, the bit-plane
+    comparison, the neighbour adder) and the FMA-heavy pipe (the Philox 32x32->64
+    products, 4 pipe cycles each).  The binding unit is the one with more busy cycles
+    per site in the committed ncu record (sm__pipe_*_cycles_active.sum, summed over the
+    4 scheduler pipes of every SM, with a hash of the kernel's sources); `achieved` is
+    those busy cycles x 16 lanes per site x sites per launch / CUDA-event time per
+    launch, against 64 lanes/clk/SM x SMs x the maximum SM clock, i.e. the pipe's
+    utilisation during the timed run.  Records without pipe cycles fall back to the
+    executed ALU-pipe operations.  The other pipe, the instruction-issue view (128
+    thread slots/clk/SM) and the HBM view ride along."""
     c = committed_counters(kernel)
     alu_peak = ALU_OPS_PER_CLK_SM * N_SMS * sm_max * 1e6 / 1e12
     issue_peak = ISSUE_SLOTS_PER_CLK_SM * N_SMS * sm_max * 1e6 / 1e12
     hbm_bytes = BYTES_PER_SITE_SWEEP * sites_per_launch
     out = {"bound": "alu", "achieved": None, "peak": alu_peak, "unit": "Tops/s", "frac": None, "traffic": None,
-           "peak_basis": f"ALU pipe: 4 schedulers x 16 lanes = {ALU_OPS_PER_CLK_SM:.0f} thread operations/clk/SM x "
-                         f"{N_SMS} SMs x {sm_max:.0f} MHz (the probe in this line measures the lanes per clock)",
+           "peak_basis": f"4 schedulers x 16 lanes = {ALU_OPS_PER_CLK_SM:.0f} lane-operations/clk/SM per integer "
+                         f"pipe x {N_SMS} SMs x {sm_max:.0f} MHz (the probe in this line measures the lanes per "
+                         f"clock)",
            "hbm_achieved_gbs": hbm_bytes / t_launch_s / 1e9, "hbm_peak_gbs": peaks.get("hbm_gbs", 6800.0)}
     if c is not None:
         out["counters"] = "current" if c["current"] else "stale: kernel source changed after the capture"
         if c["current"]:
             out["traffic"] = c["dram_bytes_per_site"] * sites_per_launch
-        if c["alu_ops_per_site"] is not None:
+        if c.get("pipe_cycles_per_site"):
+            views = {}
+            for name, cyc in c["pipe_cycles_per_site"].items():
+                ach = 16.0 * cyc * sites_per_launch / t_launch_s / 1e12
+                views[name] = {"achieved": ach, "frac": ach / alu_peak, "busy_cycles_per_site": cyc}
+            pipe = max(views, key=lambda k: views[k]["frac"])
+            out["pipe"] = PIPE_NAMES[pipe]
+            out["achieved"] = views[pipe]["achieved"]
+            out["frac"] = views[pipe]["frac"]
+            out["pipe_views"] = {PIPE_NAMES[k]: v for k, v in views.items()}
+            if c["alu_ops_per_site"] is not None:
+                out["alu_ops_per_site"] = c["alu_ops_per_site"]
+        elif c["alu_ops_per_site"] is not None:
+            out["pipe"] = PIPE_NAMES["alu"] + ", counted as executed operations"
             out["achieved"] = c["alu_ops_per_site"] * sites_per_launch / t_launch_s / 1e12
             out["frac"] = out["achieved"] / alu_peak
             out["alu_ops_per_site"] = c["alu_ops_per_site"]
@@ -616,7 +643,10 @@ def main() -> None:
     kernel = ising.PACKED if args.kernel == "packed" else ising.INT8
     seed = cfg.seed + rank
     stream = torch.cuda.Stream()
+    t_setup = time.perf_counter()
     lat = ising.Lattice(L, cfg.beta, seed, cfg.start, kernel, stream=stream)
+    t_setup = time.perf_counter() - t_setup
+    specialized, kernel_note = lat.specialized()
     lat.sweep(args.warmup)
     lat.synchronize()
     N = L * L
@@ -677,6 +707,10 @@ def main() -> None:
                        "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
                        "l2": "inputs larger than L2 (512 MB planes vs 129 MB L2), no flush"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
+            "kernel": {"specialized": specialized, "note": kernel_note, "handle_setup_s": round(t_setup, 3),
+                       "basis": "the sweep kernel compiled for this lattice's thresholds when the handle is "
+                                "created (NVRTC, once per threshold pair and process, outside the timed region; "
+                                "handle_setup_s includes it)"},
         }))
     if dist:
         dist.destroy_process_group()

@@ -189,6 +189,31 @@ int ising_load(ising_t *out, const void *buf, int64_t bytes, void *stream);
 /* Waits for the handle's work; reports ETIMEOUT if a kernel gave up. */
 int ising_synchronize(ising_t h);
 
+/*
+ * Kernels compiled for a lattice's thresholds.  The acceptance test compares each
+ * site's uniform with T_h bit plane by bit plane (Sec. 3.1's acceptance rule as an
+ * integer comparison); compiled with T_2 and T_4 as constants, each plane needs one
+ * to three logic operations instead of four, and the whole sweep about a fifth less
+ * time at the critical point.  A packed single handle of L > 256 can have its sweep
+ * kernel compiled that way (NVRTC, a few seconds, once per threshold pair and
+ * process) when it is created; the chain is the same bit for bit.
+ *
+ * ising_set_specialize sets the process-wide mode for handles created afterwards:
+ * ISING_SPECIALIZE_OFF (never), ISING_SPECIALIZE_AUTO (default: sides L >= 16384,
+ * where the compile is repaid within some thousands of sweeps) or
+ * ISING_SPECIALIZE_ALWAYS.  Where NVRTC or the compile is unavailable the handle
+ * uses the built-in kernel.  Errors: EINVAL (mode).
+ *
+ * ising_specialized: *specialized = 1 when the handle sweeps with a specialised
+ * kernel, else 0; note (may be NULL) receives a NUL-terminated reason of at most
+ * len bytes.  Host-only, does not synchronise.  Errors: EINVAL (null handle).
+ */
+#define ISING_SPECIALIZE_OFF 0
+#define ISING_SPECIALIZE_AUTO 1
+#define ISING_SPECIALIZE_ALWAYS 2
+int ising_set_specialize(int32_t mode);
+int ising_specialized(ising_t h, int32_t *specialized, char *note, int64_t len);
+
 /* Releases the handle and its device memory (NULL is a no-op).  Paper: none (resource
  * management of the Sec. 3 lattice). */
 int ising_free(ising_t h);

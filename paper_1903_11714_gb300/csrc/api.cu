@@ -3,6 +3,7 @@
 // sweep runs in the kernels of sweep_packed.cu, sweep_int8.cu, lattice_ops.cu
 // and moments.cu.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -14,6 +15,7 @@
 #include "ising.h"
 #include "arena.h"
 #include "ising_internal.cuh"
+#include "jit.h"
 #include "sweep3d.cuh"
 
 using namespace ising;
@@ -59,6 +61,12 @@ constexpr int64_t kMaxSweeps = 0xFFFFFFFEll;  // sweep counter is a 32-bit Philo
 // Handle kind of a cubic (3D) lattice; the public kernel ids are ISING_PACKED
 // and ISING_INT8 (2D).
 constexpr int kKernelCubic = 2;
+
+// Kernels compiled for a lattice's thresholds (jit.cu): process-wide mode, and the
+// smallest side the automatic mode specialises (a compile of a few seconds is then
+// repaid within some thousands of sweeps).
+std::atomic<int> g_specialize{ISING_SPECIALIZE_AUTO};
+constexpr int64_t kSpecializeMinL = 16384;
 
 // Acceptance thresholds T_h = min(2^32, ceil(exp(-2 beta h) 2^32)), h = 2, 4
 // (and h = 6 when n = 3, for the cubic lattice).
@@ -197,6 +205,9 @@ struct Engine {
     const LatticeDesc* one = nullptr;
     bool capturing = false;
     bool one_lattice = false;  // launches the single-lattice instance (sizes the grid by its occupancy)
+    // single-lattice handles: the instance compiled for the lattice's thresholds (jit.cu),
+    // used for the by-value launches; nullptr: the built-in instance
+    const void* fixed = nullptr;
     bool blocks = false;       // some lattice has column-block tiles (launch the build that handles them)
 
     void allow_blocks()
@@ -205,9 +216,11 @@ struct Engine {
         blocks = true;
     }
 
-    int setup(int max_count_, int stage_bytes_, int threads_, cudaStream_t s, bool one_lattice_ = false)
+    int setup(int max_count_, int stage_bytes_, int threads_, cudaStream_t s, bool one_lattice_ = false,
+              const void* fixed_ = nullptr)
     {
         one_lattice = one_lattice_;
+        fixed = fixed_;
         max_count = max_count_;
         stage_bytes = (stage_bytes_ + 15) / 16 * 16;
         threads = threads_;
@@ -229,6 +242,12 @@ struct Engine {
         CK(packed_set_smem_limit(threads, smem));
         int per_sm = 0;
         CK(packed_occupancy(threads, smem, &per_sm, one_lattice));
+        if (fixed) {
+            // the grid follows the instance the plain launches use
+            int per_sm_fixed = 0;
+            CK(packed_fixed_configure(fixed, smem, threads, &per_sm_fixed));
+            per_sm = per_sm_fixed;
+        }
         if (per_sm < 1) return fail(ISING_EINVAL, "sweep kernel does not fit: %d threads, %zu B smem", threads, smem);
         grid = per_sm * sm_count();
         drop_graph();
@@ -274,7 +293,8 @@ struct Engine {
         for (int64_t k = 0; k < n; ++k) {
             for (int c = 0; c < 2; ++c) {
                 cudaError_t e = launch_packed_half_sweep(tt, c, (int)k, d_status, grid, threads, stage_bytes, stream,
-                                                         kWaitLimitCycles, 0u, by_value, blocks);
+                                                         kWaitLimitCycles, 0u, by_value, blocks,
+                                                         by_value ? fixed : nullptr);
                 if (e != cudaSuccess) return cuda_fail(e, "packed half-sweep launch");
             }
         }
@@ -392,6 +412,7 @@ struct ising_s {
     int64_t* d_me0 = nullptr;   // start-state (M, E)
     double* d_mom = nullptr;    // 6 doubles
     uint64_t* d_sums = nullptr; // 11 limbs
+    std::string kernel_note;    // which sweep kernel runs, and why (ising_specialized)
 };
 
 struct ising_batch_s {
@@ -676,7 +697,22 @@ int ising_init_ex(ising_t* out, int64_t L, double beta, uint64_t seed, int start
         d.sweep = 0;
         d.target = kNoTarget;
         d.active = 1;
-        rc = h->eng.setup(1, (int)stage_bytes_for(L, tr, cw), 256, h->stream, true);
+        // the sweep kernel: the resident one for small sides, else the tiled one, compiled
+        // for this lattice's thresholds where the mode asks for it and it can be had
+        const void* fixed = nullptr;
+        const int mode = g_specialize.load();
+        if (L <= packed_resident_max_L()) {
+            h->kernel_note = "built-in: single-CTA resident kernel (L <= 256)";
+        } else if (mode == ISING_SPECIALIZE_OFF) {
+            h->kernel_note = "built-in: specialisation switched off";
+        } else if (mode == ISING_SPECIALIZE_AUTO && L < kSpecializeMinL) {
+            h->kernel_note = "built-in: L below 16384 (automatic mode)";
+        } else {
+            std::string why;
+            fixed = jit_sweep_kernel(256, cw != (int)(L / 64), d.t2, d.t4, d.all2, d.all4, &why);
+            h->kernel_note = fixed ? "specialised: compiled for this lattice's thresholds" : "built-in: " + why;
+        }
+        rc = h->eng.setup(1, (int)stage_bytes_for(L, tr, cw), 256, h->stream, true, fixed);
         if (rc) {
             destroy_handle(h);
             return rc;
@@ -710,6 +746,28 @@ int ising_init_ex(ising_t* out, int64_t L, double beta, uint64_t seed, int start
         return rc;
     }
     *out = h;
+    return ISING_OK;
+}
+
+int ising_set_specialize(int32_t mode)
+{
+    if (mode != ISING_SPECIALIZE_OFF && mode != ISING_SPECIALIZE_AUTO && mode != ISING_SPECIALIZE_ALWAYS)
+        return fail(ISING_EINVAL, "mode must be ISING_SPECIALIZE_OFF, _AUTO or _ALWAYS");
+    g_specialize.store(mode);
+    return ISING_OK;
+}
+
+int ising_specialized(ising_t h, int32_t* specialized, char* note, int64_t len)
+{
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (specialized) *specialized = h->eng.fixed ? 1 : 0;
+    if (note && len > 0) {
+        const std::string& n = h->kernel_note.empty() ? std::string("built-in") : h->kernel_note;
+        const size_t k = std::min<size_t>(n.size(), (size_t)len - 1);
+        memcpy(note, n.data(), k);
+        note[k] = '\0';
+    }
     return ISING_OK;
 }
 

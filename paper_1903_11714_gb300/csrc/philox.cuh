@@ -22,7 +22,7 @@
 // are formed once per (sweep, colour, q high) and 16 per call remain, without
 // changing a single output bit.
 #pragma once
-#include <cstdint>
+#include "ising_device.cuh"
 
 namespace ising {
 

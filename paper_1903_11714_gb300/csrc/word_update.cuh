@@ -3,7 +3,7 @@
 // tiled sweep kernel, the single-CTA resident kernel, the int8 kernel and the
 // three-dimensional sweep.
 #pragma once
-#include <cstdint>
+#include "ising_device.cuh"
 
 #include "philox.cuh"
 
@@ -28,8 +28,10 @@ namespace ising {
 // Calls C0 .. C1-1 (planes 4*C0 .. 4*C1-1) are drawn; sites still in und after
 // call 7 are not below (U equals T).  VOTE: stop when no site of the whole warp is
 // undecided (every lane of the warp must be present), else when none of this
-// thread's is.
-template <int G, int NTH, int C0 = 0, int C1 = 8, bool VOTE = false>
+// thread's is.  CHECK = false draws every call without that test: for calls that
+// nearly every warp needs, so that the calls and their comparisons form one block
+// of straight-line code whose multiplies and logic operations can interleave.
+template <int G, int NTH, int C0 = 0, int C1 = 8, bool VOTE = false, bool CHECK = true>
 __device__ __forceinline__ void bitsliced_below(uint32_t und[G], uint32_t lt[G], const uint32_t selA[G],
                                                 const uint32_t selB[G], const uint32_t q_lo[G],
                                                 const PhiloxWordConsts& pc, uint64_t key, const uint32_t (&t)[NTH])
@@ -42,7 +44,7 @@ __device__ __forceinline__ void bitsliced_below(uint32_t und[G], uint32_t lt[G],
         uint32_t any = 0;
 #pragma unroll
         for (int k = 0; k < G; ++k) any |= und[k];
-        if (VOTE ? !__any_sync(0xffffffffu, any != 0u) : any == 0u) break;
+        if (CHECK && (VOTE ? !__any_sync(0xffffffffu, any != 0u) : any == 0u)) break;
         uint32_t o[G][4];
         philox_calls<G>(base, (uint32_t)c, pc, key, o);
 #pragma unroll

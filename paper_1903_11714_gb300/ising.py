@@ -75,6 +75,8 @@ _SIGS = {
     "ising_dev_philox": (ctypes.c_int, [_u64, _P(ctypes.c_uint32), _i64, _vp, _vp]),
     "ising_probe_int_rates": (ctypes.c_int, [_P(_d)]),
     "ising_selftest_timeout": (ctypes.c_int, [_i64, _P(ctypes.c_int)]),
+    "ising_set_specialize": (ctypes.c_int, [_i32]),
+    "ising_specialized": (ctypes.c_int, [_vp, _P(_i32), ctypes.c_char_p, _i64]),
     "ising_sweep_packed_noalloc": (ctypes.c_int, [_i32, _P(_vp), _P(_vp), _P(_i64), _P(_d), _P(_u64), _i64, _i64,
                                                   _P(_vp), _vp, _i32]),
 }
@@ -211,6 +213,22 @@ def ising_batch_observables(b: int, idx: int) -> tuple[int, int]:
     M, E = ctypes.c_int64(), ctypes.c_int64()
     _check(lib().ising_batch_observables(b, int(idx), ctypes.byref(M), ctypes.byref(E)))
     return M.value, E.value
+
+
+SPECIALIZE_OFF, SPECIALIZE_AUTO, SPECIALIZE_ALWAYS = 0, 1, 2
+
+
+def ising_set_specialize(mode: int) -> None:
+    """Process-wide: whether handles created afterwards sweep with a kernel compiled
+    for their thresholds (SPECIALIZE_OFF, _AUTO (default), _ALWAYS)."""
+    _check(lib().ising_set_specialize(int(mode)))
+
+
+def ising_specialized(h: int) -> tuple[bool, str]:
+    flag = ctypes.c_int32()
+    buf = ctypes.create_string_buffer(256)
+    _check(lib().ising_specialized(h, ctypes.byref(flag), buf, len(buf)))
+    return bool(flag.value), buf.value.decode()
 
 
 def ising_thresholds3d(beta: float) -> tuple[int, int, int]:
@@ -375,6 +393,10 @@ class Lattice:
 
     def synchronize(self) -> None:
         ising_synchronize(self.h)
+
+    def specialized(self) -> tuple[bool, str]:
+        """(True, note) when the sweeps run a kernel compiled for this lattice's thresholds."""
+        return ising_specialized(self.h)
 
     def close(self) -> None:
         if self.h:

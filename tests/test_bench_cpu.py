@@ -3,9 +3,11 @@
 * The counter records are tied to the kernel sources by a hash of the code
   without comments, so a comment edit keeps a record current and a code edit
   makes it stale (string literals, which hold inline PTX, count as code).
-* `achieved` = ALU-pipe thread operations per site x sites per launch / launch
-  time, against 64 lanes per clock per SM x 152 SMs x the SM clock; `traffic` is
-  the record's DRAM bytes per site x sites, and null once the record is stale.
+* `achieved` = the busier integer pipe's busy cycles x 16 lanes per site x sites
+  per launch / launch time (or, for records without pipe cycles, the executed
+  ALU-pipe operations), against 64 lanes per clock per SM x 152 SMs x the SM clock;
+  `traffic` is the record's DRAM bytes per site x sites, and null once the record is
+  stale.
 """
 import json
 import os
@@ -40,7 +42,7 @@ def test_every_counter_record_names_its_capture(kernel):
 
 
 def fake_counters(current):
-    return {"current": current, "inst_slots_per_site": 6.0, "alu_ops_per_site": 3.5,
+    return {"current": current, "inst_slots_per_site": 6.0, "alu_ops_per_site": 3.5, "pipe_cycles_per_site": None,
             "dram_bytes_per_site": 0.4, "capture": "ncu ..."}
 
 
@@ -60,6 +62,25 @@ def test_roofline_arithmetic(monkeypatch):
     # the HBM view: 0.375 algorithmic bytes per updated site of a half-sweep (= per site and sweep)
     assert r["hbm_achieved_gbs"] == pytest.approx(0.375 * sites / t / 1e9)
     assert r["hbm_peak_gbs"] == 6778.7
+
+
+def test_roofline_binds_on_the_busier_pipe(monkeypatch):
+    """With pipe cycles in the record, the pipe with more busy cycles per site binds:
+    achieved = 16 lanes x busy cycles x sites / time."""
+    def counters(pipes):
+        return lambda k: {**fake_counters(True), "pipe_cycles_per_site": pipes}
+
+    sites, t, mhz = 2.0 ** 31, 5.0e-4, 2070.0
+    peak = 64 * 152 * mhz * 1e6 / 1e12
+    monkeypatch.setattr(bench, "committed_counters", counters({"alu": 0.16, "fmaheavy": 0.19}))
+    r = bench.kernel_roofline("packed_half_sweep", sites, t, mhz, {})
+    assert r["pipe"].startswith("FMA-heavy")
+    assert r["achieved"] == pytest.approx(16 * 0.19 * sites / t / 1e12)
+    assert r["frac"] == pytest.approx(r["achieved"] / peak)
+    assert r["pipe_views"][bench.PIPE_NAMES["alu"]]["frac"] == pytest.approx(16 * 0.16 * sites / t / 1e12 / peak)
+    monkeypatch.setattr(bench, "committed_counters", counters({"alu": 0.21, "fmaheavy": 0.12}))
+    r = bench.kernel_roofline("packed_half_sweep", sites, t, mhz, {})
+    assert r["pipe"].startswith("ALU") and r["achieved"] == pytest.approx(16 * 0.21 * sites / t / 1e12)
 
 
 def test_stale_counters_null_the_traffic(monkeypatch):

@@ -33,15 +33,24 @@ def _lib():
 def packed_run():
     cfg = workloads.single_large()
     lat = ising.Lattice(cfg.L, cfg.beta, cfg.seed, cfg.start, ising.PACKED)
+    specialized = lat.specialized()
     lat.sweep(cfg.sweeps)
     M, E = lat.history()
     s = lat.get_lattice()
     lat.close()
-    return cfg, s, M, E
+    return cfg, s, M, E, specialized
+
+
+def test_the_benchmarked_lattice_runs_the_specialised_kernel(packed_run):
+    """The default (automatic) mode compiles this lattice's sweep kernel for its
+    thresholds -- the kernel the benchmark times -- and the other tests in this file
+    check that kernel's chain."""
+    specialized, note = packed_run[4]
+    assert specialized, note
 
 
 def test_windows_match_oracle_light_cone(packed_run):
-    cfg, s, M, E = packed_run
+    cfg, s, M, E = packed_run[:4]
     L = cfg.L
     rng = np.random.default_rng(2024)
     spots = [(0, 0), (L - 3, L - 40), (L // 2, 64 * 511 + 7)] + [
@@ -55,7 +64,7 @@ def test_windows_match_oracle_light_cone(packed_run):
 
 
 def test_invariants(packed_run):
-    cfg, s, M, E = packed_run
+    cfg, s, M, E = packed_run[:4]
     N = cfg.L ** 2
     assert np.all(E % 4 == 0) and np.all(np.abs(E) <= 2 * N)
     assert np.all(M % 2 == 0) and np.all(np.abs(M) <= N)
@@ -65,7 +74,7 @@ def test_invariants(packed_run):
 def test_matches_golden(packed_run):
     if not os.path.exists(GOLDEN):
         pytest.skip("golden file for L = 65,536 not generated")
-    cfg, s, M, E = packed_run
+    cfg, s, M, E = packed_run[:4]
     g = json.load(open(GOLDEN))
     assert g["workload"] == cfg.as_dict()
     assert M.tolist() == g["M"] and E.tolist() == g["E"]
@@ -73,7 +82,7 @@ def test_matches_golden(packed_run):
 
 
 def test_int8_kernel_agrees_at_full_size(packed_run):
-    cfg, s, M, E = packed_run
+    cfg, s, M, E = packed_run[:4]
     lat = ising.Lattice(cfg.L, cfg.beta, cfg.seed, cfg.start, ising.INT8)
     lat.sweep(cfg.sweeps)
     M8, E8 = lat.history()

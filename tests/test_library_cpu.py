@@ -343,3 +343,15 @@ def test_noalloc_lattice_arguments(lib):
     assert call([256], count=0) == ising.ISING_EINVAL
     assert call([256] * 65) == ising.ISING_EINVAL
     assert call([256] * 64) == ising.ISING_ECUDA
+
+
+def test_specialize_mode_arguments(lib):
+    """ising_set_specialize takes OFF, AUTO or ALWAYS only; ising_specialized needs a
+    handle.  Both are host-only."""
+    for mode in (ising.SPECIALIZE_OFF, ising.SPECIALIZE_ALWAYS, ising.SPECIALIZE_AUTO):
+        assert lib.ising_set_specialize(mode) == ising.ISING_OK
+    for mode in (-1, 3, 100):
+        assert lib.ising_set_specialize(mode) == ising.ISING_EINVAL
+    flag = ctypes.c_int32(7)
+    assert lib.ising_specialized(None, ctypes.byref(flag), None, 0) == ising.ISING_EINVAL
+    assert flag.value == 7

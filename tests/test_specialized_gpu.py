@@ -1,0 +1,80 @@
+"""GPU parity of the sweep kernel compiled for a lattice's thresholds.
+
+A packed single handle can sweep with the tiled kernel compiled (NVRTC, at handle
+creation) with its thresholds T_2, T_4 as constants, so that each bit plane of the
+uniforms is compared with the logic its threshold bits need.  The chain must not
+change: with the mode forced on, lattices of every row-width class (words per row
+divisible by 4, odd, 2 mod 4) and the degenerate temperatures (beta = 0, where
+T = 2^32 and every site flips; beta = 200, where T = 0 and only h <= 0 flips)
+match the oracle's lattice and per-sweep M and E, and the built-in kernel's.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1903_11714_gb300 import build as libbuild
+from paper_1903_11714_gb300 import ising
+
+pytestmark = pytest.mark.gpu
+
+CASES = [(320, 0.4406868, 21, ising.HOT, 12),   # W = 5 (odd): one word per thread group
+         (384, 0.30, 22, ising.HOT, 9),          # W = 6 (2 mod 4): two words
+         (512, 0.55, 23, ising.COLD, 10),        # W = 8: four words
+         (1024, 0.4406868, 24, ising.HOT, 25),
+         (576, 0.0, 25, ising.HOT, 4),           # T_2 = T_4 = 2^32: every site flips
+         (640, 200.0, 26, ising.HOT, 6)]         # T_2 = T_4 = 0: only h <= 0 flips
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    libbuild.build()
+    ising.lib()
+    yield
+    ising.ising_set_specialize(ising.SPECIALIZE_AUTO)
+
+
+@pytest.mark.parametrize("L,beta,seed,start,sweeps", CASES)
+def test_specialised_kernel_matches_oracle_and_built_in(L, beta, seed, start, sweeps):
+    ref, Mr, Er, _ = oracle.run(L, beta, seed, start, sweeps)
+    got = {}
+    for mode in (ising.SPECIALIZE_ALWAYS, ising.SPECIALIZE_OFF):
+        ising.ising_set_specialize(mode)
+        lat = ising.Lattice(L, beta, seed, start, ising.PACKED)
+        spec, note = lat.specialized()
+        assert spec == (mode == ising.SPECIALIZE_ALWAYS), note
+        lat.sweep(sweeps)
+        M, E = lat.history()
+        got[mode] = lat.get_lattice()
+        lat.close()
+        assert np.array_equal(got[mode], ref), (mode, note)
+        assert np.array_equal(M, Mr) and np.array_equal(E, Er), mode
+    ising.ising_set_specialize(ising.SPECIALIZE_AUTO)
+
+
+def test_automatic_mode_leaves_small_lattices_built_in():
+    ising.ising_set_specialize(ising.SPECIALIZE_AUTO)
+    for L in (128, 1024, 8192):
+        lat = ising.Lattice(L, 0.44, 1, ising.HOT, ising.PACKED)
+        spec, note = lat.specialized()
+        lat.close()
+        assert not spec and note.startswith("built-in"), (L, note)
+
+
+def test_specialised_chain_continues_across_calls_and_checkpoints():
+    """Sweeps split over several calls, and a checkpoint taken mid-way and resumed
+    in a new (again specialised) handle, give the single run's chain."""
+    L, beta, seed, n = 768, 0.47, 31, 14
+    ising.ising_set_specialize(ising.SPECIALIZE_ALWAYS)
+    ref, Mr, Er, _ = oracle.run(L, beta, seed, ising.HOT, n)
+    lat = ising.Lattice(L, beta, seed, ising.HOT, ising.PACKED)
+    lat.sweep(3).sweep(4)
+    blob = lat.save()
+    lat.close()
+    lat2 = ising.Lattice.load(blob)
+    assert lat2.specialized()[0]
+    lat2.sweep(n - 7)
+    M, E = lat2.history()
+    assert np.array_equal(lat2.get_lattice(), ref)
+    assert np.array_equal(M, Mr) and np.array_equal(E, Er)
+    lat2.close()
+    ising.ising_set_specialize(ising.SPECIALIZE_AUTO)
