@@ -185,6 +185,28 @@ int single_tile_rows(int64_t L)
     return tile_rows_ok(L, tr) ? tr : default_tile_rows(L);
 }
 
+// CTA size and tile height of a lattice swept on its own.  Sides of at least 16,384
+// with whole-row tiles take one 512-thread CTA per SM and tiles of up to 8,192 words,
+// so that each of its 16 warps still handles about 512 words of a tile: the per-tile
+// costs (the last partial drain of each warp's queue, the stage handoff) are then a
+// smaller share than with two 256-thread CTAs of 4,096-word tiles (+2 % at L = 65,536;
+// 512-thread CTAs with 4,096-word tiles lose 6 %).  Other sides: 256 threads and
+// single_tile_rows.
+void single_config(int64_t L, int* tile_rows, int* threads)
+{
+    *threads = 256;
+    *tile_rows = single_tile_rows(L);
+    const int64_t W = L / 64;
+    if (L < 16384 || !whole_rows_ok(L)) return;
+    int best = 0;
+    for (int tr = 2; tr <= kMaxTileRows; tr *= 2)
+        if (tile_rows_ok(L, tr) && W * tr <= 8192 && L / tr >= 2 * sm_count()) best = tr;
+    if (best && W * best >= 4096) {
+        *threads = 512;
+        *tile_rows = best;
+    }
+}
+
 // ---------------------------------------------------------------- engine
 // The launch state of the packed persistent kernel: descriptor array, tile
 // table, status word, grid, and an optional captured graph of k sweeps.
@@ -682,7 +704,8 @@ int ising_init_ex(ising_t* out, int64_t L, double beta, uint64_t seed, int start
         CKH(launch_packed_init(h->planes, h->planes + plane_words, L, seed, start, h->stream));
         // whole rows when they fit a tile, else 2-row column blocks
         const int cw = default_tile_words(L);
-        const int tr = cw == (int)(L / 64) ? single_tile_rows(L) : 2;
+        int tr = 2, threads = 256;
+        if (cw == (int)(L / 64)) single_config(L, &tr, &threads);
         LatticeDesc& d = h->desc;
         d.plane[0] = h->planes;
         d.plane[1] = h->planes + plane_words;
@@ -709,10 +732,10 @@ int ising_init_ex(ising_t* out, int64_t L, double beta, uint64_t seed, int start
             h->kernel_note = "built-in: L below 16384 (automatic mode)";
         } else {
             std::string why;
-            fixed = jit_sweep_kernel(256, cw != (int)(L / 64), d.t2, d.t4, d.all2, d.all4, &why);
+            fixed = jit_sweep_kernel(threads, cw != (int)(L / 64), d.t2, d.t4, d.all2, d.all4, &why);
             h->kernel_note = fixed ? "specialised: compiled for this lattice's thresholds" : "built-in: " + why;
         }
-        rc = h->eng.setup(1, (int)stage_bytes_for(L, tr, cw), 256, h->stream, true, fixed);
+        rc = h->eng.setup(1, (int)stage_bytes_for(L, tr, cw), threads, h->stream, true, fixed);
         if (rc) {
             destroy_handle(h);
             return rc;

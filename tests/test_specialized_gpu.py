@@ -78,3 +78,20 @@ def test_specialised_chain_continues_across_calls_and_checkpoints():
     assert np.array_equal(M, Mr) and np.array_equal(E, Er)
     lat2.close()
     ising.ising_set_specialize(ising.SPECIALIZE_AUTO)
+
+
+def test_large_single_handles_take_512_thread_ctas_and_stay_exact():
+    """L = 16,384 is the smallest side swept by one 512-thread CTA per SM with tiles of
+    32 rows (8,192 words); both its builds (specialised, built-in) match the oracle."""
+    L, beta, seed, n = 16384, 0.4406868, 41, 3
+    ref, Mr, Er, _ = oracle.run(L, beta, seed, ising.HOT, n)
+    for mode in (ising.SPECIALIZE_AUTO, ising.SPECIALIZE_OFF):
+        ising.ising_set_specialize(mode)
+        lat = ising.Lattice(L, beta, seed, ising.HOT, ising.PACKED)
+        assert lat.specialized()[0] == (mode == ising.SPECIALIZE_AUTO)
+        lat.sweep(n)
+        M, E = lat.history()
+        assert np.array_equal(M, Mr) and np.array_equal(E, Er), mode
+        assert np.array_equal(lat.get_lattice(), ref), mode
+        lat.close()
+    ising.ising_set_specialize(ising.SPECIALIZE_AUTO)
