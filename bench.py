@@ -302,7 +302,7 @@ def _events(torch, stream):
     return e0, e1
 
 
-def run_single_small(args) -> None:
+def run_single_small(args) -> dict:
     """L = 128, 1000 sweeps: packed (one resident CTA for all sweeps, bound by that
     one SM) vs plain int8 (two launches per sweep, launch-latency bound)."""
     import torch
@@ -324,12 +324,13 @@ def run_single_small(args) -> None:
         ms = e0.elapsed_time(e1)
         lat.close()
         out[name] = cfg.sweeps * cfg.L ** 2 / (ms * 1e6)
-    print(json.dumps({"metric": "spin-flip attempts/ns, L=128 single lattice", "workload": "single_small",
-                      "unit": UNIT, "value": out["packed"], "int8_value": out["int8"],
-                      "config": cfg.as_dict(), "note": "packed: one single-CTA launch for all sweeps; int8: 2 launches per sweep (launch-latency bound)"}))
+    return {"metric": "spin-flip attempts/ns, L=128 single lattice", "workload": "single_small",
+            "unit": UNIT, "value": out["packed"], "plain_int8_value": out["int8"], "basis": "CUDA events",
+            "config": cfg.as_dict(),
+            "note": "packed: one single-CTA launch for all sweeps; int8: 2 launches per sweep (launch-latency bound)"}
 
 
-def run_batched(args, which: str) -> None:
+def run_batched(args, which: str) -> dict:
     """Batched forms (one persistent launch per half-sweep over all lattices)
     against plain launches of the int8 and packed kernels, one lattice at a time."""
     import torch
@@ -388,12 +389,13 @@ def run_batched(args, which: str) -> None:
             total_ms += a0.elapsed_time(a1)
             lat.close()
         plain[name] = n_plain * sum(l.L * l.L for l in lats) / (total_ms * 1e6)
-    print(json.dumps({"metric": f"aggregate spin-flip attempts/ns, {which} batch", "workload": which,
-                      "unit": UNIT, "value": batched, "plain_int8_value": plain["int8"],
-                      "plain_packed_value": plain["packed"], "lattices": len(lats), "sweeps": sweeps,
-                      "graph_sweeps": graph, "ms": ms,
-                      "tile_rows_by_L": tiles or None, "threads": threads,
-                      "note": f"plain = each lattice alone with its own launches, {n_plain} sweeps each"}))
+    return {"metric": f"aggregate spin-flip attempts/ns, {which} batch", "workload": which,
+            "unit": UNIT, "value": batched, "plain_int8_value": plain["int8"],
+            "plain_packed_value": plain["packed"], "lattices": len(lats), "sweeps": sweeps,
+            "graph_sweeps": graph, "ms": ms, "basis": "CUDA events on the batch's stream",
+            "tile_rows_by_L": tiles or None, "threads": threads,
+            "note": f"batched = one persistent launch per half-sweep over all lattices, a CUDA graph of {graph} "
+                    f"sweeps replayed; plain = each lattice alone with its own launches, {n_plain} sweeps each"}
 
 
 def run_cubic(args) -> None:
@@ -547,7 +549,7 @@ def run_binder(args) -> None:
                       "abs_m": {str(L): [[round(t, 4), m] for t, _, m, _ in sorted(v)] for L, v in table.items()}}))
 
 
-def run_serve(args) -> None:
+def run_serve(args) -> dict:
     """Poisson arrivals at ~80 % of measured capacity; p50/p99 latency."""
     import torch
 
@@ -570,14 +572,15 @@ def run_serve(args) -> None:
     results, st_ = srv.serve(reqs, realtime=True)
     srv.close()
     summ = st_.summary()
-    print(json.dumps({"metric": "serving: p50/p99 latency and aggregate spin-flip attempts/ns",
-                      "workload": "serve", "unit": UNIT, "value": summ["flips_per_ns"],
-                      "p50_s": summ["p50_s"], "p99_s": summ["p99_s"], "requests": summ["completed"],
-                      "rate_per_s": rate, "capacity_flips_per_ns": capacity / 1e9,
-                      "mean_request_flips": mean_flips, "hbm_budget_gb": args.serve_budget_gb,
-                      "slots": args.serve_slots, "quantum_sweeps": args.serve_quantum, "threads": threads,
-                      "max_active": summ["max_active"], "max_arena_gb": summ["max_arena_bytes"] / 2**30,
-                      "blocked_by_memory": summ["blocked_by_memory"], "blocked_by_slots": summ["blocked_by_slots"]}))
+    return {"metric": "serving: p50/p99 latency and aggregate spin-flip attempts/ns",
+            "workload": "serve", "unit": UNIT, "value": summ["flips_per_ns"], "basis": "wall clock, real-time arrivals",
+            "p50_s": summ["p50_s"], "p99_s": summ["p99_s"], "requests": summ["completed"],
+            "rate_per_s": rate, "capacity_flips_per_ns": capacity / 1e9,
+            "mean_request_flips": mean_flips, "hbm_budget_gb": args.serve_budget_gb,
+            "slots": args.serve_slots, "quantum_sweeps": args.serve_quantum or "adaptive (8..256)",
+            "threads": threads, "quanta": summ["quanta"],
+            "max_active": summ["max_active"], "max_arena_gb": summ["max_arena_bytes"] / 2**30,
+            "blocked_by_memory": summ["blocked_by_memory"], "blocked_by_slots": summ["blocked_by_slots"]}
 
 
 def make_parser() -> argparse.ArgumentParser:
@@ -603,7 +606,12 @@ def make_parser() -> argparse.ArgumentParser:
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--serve-calib", type=int, default=150)
     ap.add_argument("--serve-slots", type=int, default=256)
-    ap.add_argument("--serve-quantum", type=int, default=32)
+    ap.add_argument("--serve-quantum", type=int, default=0, help="sweeps per quantum; 0 = adaptive")
+    ap.add_argument("--no-sub", action="store_true",
+                    help="default run: skip the repeats and the records of configurations 1, 3, 4, 5 and int8")
+    ap.add_argument("--repeats", type=int, default=5, help="extra timings of the K timed steps (spread)")
+    ap.add_argument("--sub-serve-requests", type=int, default=600,
+                    help="requests of the serving record appended to the default run")
     ap.add_argument("--serve-budget-gb", type=float, default=120.0)
     return ap
 
@@ -628,9 +636,10 @@ def main() -> None:
     torch.cuda.set_device(local)
     if args.workload != "single_large":
         libbuild.build()
-        {"single_small": run_single_small, "serve": run_serve, "binder": run_binder, "cubic": run_cubic,
-         "binder3d": run_binder3d}.get(
-            args.workload, lambda a: run_batched(a, args.workload))(args)
+        rec = {"single_small": run_single_small, "serve": run_serve, "binder": run_binder, "cubic": run_cubic,
+               "binder3d": run_binder3d}.get(args.workload, lambda a: run_batched(a, args.workload))(args)
+        if rec is not None:
+            print(json.dumps(rec))
         return
     dist = None
     if world > 1:
@@ -687,10 +696,42 @@ def main() -> None:
     roofline["probe_alu_ops_per_clk_sm"] = alu_per_clk
     roofline["probe_mul_xor_steps_per_clk_sm"] = mul_per_clk
 
+    # the same K timed steps again, for the run-to-run spread (the lattice continues its chain)
+    reps = []
+    for _ in range(args.repeats if not args.no_sub else 0):
+        r0 = torch.cuda.Event(enable_timing=True)
+        r1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        r0.record(stream)
+        lat.sweep(args.steps)
+        r1.record(stream)
+        torch.cuda.synchronize()
+        reps.append(args.steps * N / (r0.elapsed_time(r1) * 1e6))
+    lat.synchronize()
+    repeats = None
+    if reps:
+        allv = [value] + reps if world == 1 else reps
+        repeats = {"timings": len(allv), "values": allv, "median": statistics.median(allv), "min": min(allv),
+                   "max": max(allv), "spread_pct": 100.0 * (max(allv) - min(allv)) / statistics.median(allv),
+                   "basis": f"the {args.steps} timed steps, then {len(reps)} more timings of {args.steps} steps each "
+                            f"(CUDA events, same lattice continuing its chain)"}
+
     e2e = None
     if not args.no_e2e and kernel == ising.PACKED and rank == 0:
         e2e = measure_e2e(lat, L, cfg, args.steps, stream)
     lat.close()
+
+    # the rest of the metric ("batched vs plain; p50/p99 latency"): records of the other
+    # configurations and of the plain int8 kernel on this one, each with its own basis
+    sub = None
+    if rank == 0 and world == 1 and not args.no_sub and kernel == ising.PACKED and not args.L:
+        sub = {"config2_plain_int8": run_plain_int8(cfg, args.steps, args.warmup),
+               "config1_single_small": run_single_small(args),
+               "config3_scan": run_batched(args, "scan"),
+               "config4_uneven": run_batched(args, "uneven")}
+        sargs = argparse.Namespace(**vars(args))
+        sargs.serve_requests = args.sub_serve_requests
+        sub["config5_serve"] = run_serve(sargs)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -707,6 +748,7 @@ def main() -> None:
                        "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
                        "l2": "inputs larger than L2 (512 MB planes vs 129 MB L2), no flush"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
+            "repeats": repeats, "sub": sub,
             "kernel": {"specialized": specialized, "note": kernel_note, "handle_setup_s": round(t_setup, 3),
                        "basis": "the sweep kernel compiled for this lattice's thresholds when the handle is "
                                 "created (NVRTC, once per threshold pair and process, outside the timed region; "
@@ -714,6 +756,30 @@ def main() -> None:
         }))
     if dist:
         dist.destroy_process_group()
+
+
+def run_plain_int8(cfg, steps: int, warmup: int) -> dict:
+    """The plain int8 kernel (row-major bytes, one lattice) on the same lattice and steps."""
+    import torch
+
+    from paper_1903_11714_gb300 import ising
+
+    st = torch.cuda.Stream()
+    lat = ising.Lattice(cfg.L, cfg.beta, cfg.seed, cfg.start, ising.INT8, stream=st)
+    lat.sweep(warmup)
+    lat.synchronize()
+    e0, e1 = _events(torch, st)
+    e0.record(st)
+    lat.sweep(steps)
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    lat.close()
+    N = cfg.L * cfg.L
+    return {"metric": "spin-flip attempts/ns, plain int8 kernel", "workload": "single_large", "unit": UNIT,
+            "value": steps * N / (ms * 1e6), "steps": steps, "basis": "CUDA events",
+            "hbm_achieved_gbs": 4.0 * N * steps / (ms * 1e-3) / 1e9,
+            "note": "row-major int8 lattice (4.3 GB), each half-sweep reads and writes every byte"}
 
 
 def measure_e2e(lat, L, cfg, steps, stream) -> dict:

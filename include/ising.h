@@ -314,9 +314,12 @@ int ising_batch_remove(ising_batch_t b, int32_t idx);
 /*
  * Enqueues `sweeps` sweeps of every lattice in the batch; a lattice admitted with
  * ising_batch_add stops at its own sweep limit.  graph_sweeps (the use_graph
- * switch) > 0: capture graph_sweeps sweeps into a CUDA graph once (re-captured if
- * graph_sweeps changes) and replay it sweeps / graph_sweeps times (sweeps must be
- * a multiple, else EINVAL); 0: plain launches.  Paper: Sec. 3.1 (the sweep), Sec. 5.1.
+ * switch) > 0: capture graph_sweeps sweeps into a CUDA graph once per distinct
+ * graph_sweeps (a few are kept) and replay it sweeps / graph_sweeps times (sweeps
+ * must be a multiple, else EINVAL); 0: plain launches.  Admitting, removing and
+ * running lattices enqueue work without waiting for the stream's earlier sweeps
+ * (batches of more than 7,679 lattices wait when the tile table changes).
+ * Paper: Sec. 3.1 (the sweep), Sec. 5.1.
  */
 int ising_batch_run(ising_batch_t b, int64_t sweeps, int32_t graph_sweeps);
 
@@ -328,6 +331,18 @@ int ising_batch_sweeps_done(ising_batch_t b, int32_t idx, int64_t *sweeps_done);
  * slot); n <= capacity.  Synchronises.
  */
 int ising_batch_progress(ising_batch_t b, int64_t *sweeps_done, int32_t n);
+
+/*
+ * Without waiting: enqueues on the batch's stream a kernel that writes, for slot
+ * idx[k] (k < n), its sweeps done, M and E after its last sweep (0, 0 before any)
+ * to out[3k], out[3k+1], out[3k+2], as they stand once the work enqueued before it
+ * has run.  out: device-accessible memory of 3n int64 (device memory, or page-locked
+ * host memory the caller polls after recording an event on the stream); idx is read
+ * during the call only.  A slot may be removed right after the call (its memory is
+ * reused only by later work of the stream).  For a serving loop that keeps sweeps in
+ * flight while it collects results.  Errors: EINVAL (n, a free or bad slot), ECUDA.
+ */
+int ising_batch_gather(ising_batch_t b, int32_t n, const int32_t *idx, int64_t *out);
 
 /*
  * Slot idx: current M and E (the start state before any sweep; Sec. 4.1, Sec. 3);

@@ -220,8 +220,7 @@ struct Engine {
     int32_t* d_tile_start = nullptr;
     int32_t* d_count = nullptr;
     int* d_status = nullptr;
-    cudaGraphExec_t gexec = nullptr;
-    int g_sweeps = 0;
+    std::map<int, cudaGraphExec_t> graphs;  // captured graphs of k sweeps, by k
     // single-lattice handles: host copy of the descriptor, whose sweep field the
     // handle keeps equal to the device's; plain launches then pass it by value
     const LatticeDesc* one = nullptr;
@@ -278,19 +277,25 @@ struct Engine {
 
     void drop_graph()
     {
-        if (gexec) cudaGraphExecDestroy(gexec);
-        gexec = nullptr;
-        g_sweeps = 0;
+        for (auto& g : graphs) cudaGraphExecDestroy(g.second);
+        graphs.clear();
     }
 
+    // Descriptor and tile-table updates go by value in small kernels, ordered on the
+    // stream without waiting for its earlier work (a serving loop admits lattices while
+    // earlier sweeps run); tables too long for a few launches are copied and waited for.
     int upload_desc(int idx, const LatticeDesc& d)
     {
-        CK(cudaMemcpyAsync(d_desc + idx, &d, sizeof(LatticeDesc), cudaMemcpyHostToDevice, stream));
+        CK(launch_set_desc(d_desc + idx, d, stream));
         return ISING_OK;
     }
 
     int upload_tiles(const std::vector<int32_t>& tile_start, int32_t count)
     {
+        if (tile_start.size() <= 8 * (size_t)TileChunk::kMax) {
+            CK(launch_set_tiles(d_tile_start, d_count, tile_start.data(), (int32_t)tile_start.size(), count, stream));
+            return ISING_OK;
+        }
         CK(cudaMemcpyAsync(d_tile_start, tile_start.data(), sizeof(int32_t) * tile_start.size(),
                            cudaMemcpyHostToDevice, stream));
         CK(cudaMemcpyAsync(d_count, &count, sizeof(int32_t), cudaMemcpyHostToDevice, stream));
@@ -331,8 +336,9 @@ struct Engine {
         if (graph_sweeps <= 0) return enqueue_sweeps(sweeps);
         if (sweeps % graph_sweeps) return fail(ISING_EINVAL, "sweeps %lld not a multiple of graph_sweeps %d",
                                                (long long)sweeps, graph_sweeps);
-        if (!gexec || g_sweeps != graph_sweeps) {
-            drop_graph();
+        auto it = graphs.find(graph_sweeps);
+        if (it == graphs.end()) {
+            if (graphs.size() >= 8) drop_graph();  // a few quantum sizes are kept
             CK(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
             capturing = true;
             int rc = enqueue_sweeps(graph_sweeps);
@@ -344,12 +350,13 @@ struct Engine {
                 return rc;
             }
             if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
-            e = cudaGraphInstantiate(&gexec, g, 0);
+            cudaGraphExec_t ge = nullptr;
+            e = cudaGraphInstantiate(&ge, g, 0);
             cudaGraphDestroy(g);
             if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
-            g_sweeps = graph_sweeps;
+            it = graphs.emplace(graph_sweeps, ge).first;
         }
-        for (int64_t r = 0; r < sweeps / graph_sweeps; ++r) CK(cudaGraphLaunch(gexec, stream));
+        for (int64_t r = 0; r < sweeps / graph_sweeps; ++r) CK(cudaGraphLaunch(it->second, stream));
         return ISING_OK;
     }
 
@@ -1450,6 +1457,19 @@ int ising_batch_progress(ising_batch_t b, int64_t* sweeps_done, int32_t n)
     int rc = b->eng.check_status();
     if (rc) return rc;
     for (int32_t k = 0; k < n; ++k) sweeps_done[k] = b->slots[k].used ? (int64_t)d[k].sweep : -1;
+    return ISING_OK;
+}
+
+int ising_batch_gather(ising_batch_t b, int32_t n, const int32_t* idx, int64_t* out)
+{
+    if (!b) return fail(ISING_EINVAL, "null batch");
+    if (n < 0 || n > b->capacity) return fail(ISING_EINVAL, "n %d outside 0 .. capacity %d", n, b->capacity);
+    if (n == 0) return ISING_OK;
+    if (!idx || !out) return fail(ISING_EINVAL, "null argument");
+    for (int32_t k = 0; k < n; ++k)
+        if (idx[k] < 0 || idx[k] >= b->capacity || !b->slots[idx[k]].used)
+            return fail(ISING_EINVAL, "bad slot %d", idx[k]);
+    CK(launch_gather(b->eng.d_desc, idx, n, out, b->stream));
     return ISING_OK;
 }
 

@@ -29,6 +29,24 @@ int packed_resident_max_L();
 cudaError_t launch_packed_resident(const LatticeDesc& d, int nsweeps, cudaStream_t s);
 cudaError_t launch_packed_advance(LatticeDesc* desc, const int32_t* count, int max_count, int steps,
                                   cudaStream_t s);
+// Parameter blocks of the by-value updates (each under the 4 KB kernel-parameter limit).
+struct TileChunk {
+    static constexpr int kMax = 960;
+    int32_t first, n, count;  // entries first .. first+n-1; count >= 0: also set the lattice count
+    int32_t v[kMax];
+};
+struct GatherChunk {
+    static constexpr int kMax = 960;
+    int32_t n;
+    int32_t idx[kMax];
+};
+// Enqueue a descriptor write, a tile-table write (n entries and the lattice count), and
+// the (sweeps, M, E) gather of batch slots idx[0..n) into out[3n] (device-accessible);
+// none waits for the stream's earlier work and the host arrays may change on return.
+cudaError_t launch_set_desc(LatticeDesc* dst, const LatticeDesc& d, cudaStream_t s);
+cudaError_t launch_set_tiles(int32_t* tile_start, int32_t* count_dst, const int32_t* v, int32_t n, int32_t count,
+                             cudaStream_t s);
+cudaError_t launch_gather(const LatticeDesc* desc, const int32_t* idx, int32_t n, int64_t* out, cudaStream_t s);
 cudaError_t launch_packed_init(uint32_t* black, uint32_t* white, int64_t L, uint64_t key, int start,
                                cudaStream_t s);
 cudaError_t launch_packed_observe(const uint32_t* black, const uint32_t* white, int64_t L, int64_t* ME,

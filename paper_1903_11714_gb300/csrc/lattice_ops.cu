@@ -37,6 +37,33 @@ __global__ void set_pair_kernel(int64_t* p, int64_t a, int64_t b)
     p[1] = b;
 }
 
+// Descriptor and tile-table updates carried as kernel parameters: the parameters are
+// captured when the launch is enqueued, so the host's copy may change at once and
+// nothing waits for the stream's earlier work.
+__global__ void set_desc_kernel(LatticeDesc* dst, const LatticeDesc d)
+{
+    if (threadIdx.x == 0) *dst = d;
+}
+
+__global__ void set_tiles_kernel(int32_t* tile_start, int32_t* count_dst, const TileChunk c)
+{
+    for (int k = threadIdx.x; k < c.n; k += blockDim.x) tile_start[c.first + k] = c.v[k];
+    if (threadIdx.x == 0 && c.count >= 0) *count_dst = c.count;
+}
+
+// (sweeps done, M, E) of batch slots a.idx[0 .. a.n): M and E of the lattice's last
+// sweep, (0, 0) before any.
+__global__ void gather_kernel(const LatticeDesc* desc, const GatherChunk a, int64_t* out)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= a.n) return;
+    const LatticeDesc& d = desc[a.idx[k]];
+    const int64_t s = d.sweep;
+    out[3 * k] = s;
+    out[3 * k + 1] = s ? d.hist[2 * (s - 1)] : 0;
+    out[3 * k + 2] = s ? d.hist[2 * (s - 1) + 1] : 0;
+}
+
 // Adds 2 * (#up) and 2 * (#anti-aligned bonds) into ME (pre-set to -N, -2N).
 __global__ void packed_observe_kernel(const uint32_t* black, const uint32_t* white, int64_t L,
                                       unsigned long long* ME)
@@ -143,6 +170,39 @@ int sm_count()
         if (n <= 0) n = 1;
     }
     return n;
+}
+
+cudaError_t launch_set_desc(LatticeDesc* dst, const LatticeDesc& d, cudaStream_t s)
+{
+    set_desc_kernel<<<1, 32, 0, s>>>(dst, d);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_set_tiles(int32_t* tile_start, int32_t* count_dst, const int32_t* v, int32_t n, int32_t count,
+                             cudaStream_t s)
+{
+    int32_t first = 0;
+    do {
+        TileChunk c;
+        c.first = first;
+        c.n = n - first < TileChunk::kMax ? n - first : TileChunk::kMax;
+        c.count = first + c.n >= n ? count : -1;  // the count goes with the last chunk
+        for (int k = 0; k < c.n; ++k) c.v[k] = v[first + k];
+        set_tiles_kernel<<<1, 256, 0, s>>>(tile_start, count_dst, c);
+        first += c.n;
+    } while (first < n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather(const LatticeDesc* desc, const int32_t* idx, int32_t n, int64_t* out, cudaStream_t s)
+{
+    for (int32_t first = 0; first < n; first += GatherChunk::kMax) {
+        GatherChunk a;
+        a.n = n - first < GatherChunk::kMax ? n - first : GatherChunk::kMax;
+        for (int k = 0; k < a.n; ++k) a.idx[k] = idx[first + k];
+        gather_kernel<<<(a.n + 127) / 128, 128, 0, s>>>(desc, a, out + 3 * (int64_t)first);
+    }
+    return cudaGetLastError();
 }
 
 cudaError_t launch_packed_init(uint32_t* black, uint32_t* white, int64_t L, uint64_t key, int start, cudaStream_t s)

@@ -355,3 +355,11 @@ def test_specialize_mode_arguments(lib):
     flag = ctypes.c_int32(7)
     assert lib.ising_specialized(None, ctypes.byref(flag), None, 0) == ising.ISING_EINVAL
     assert flag.value == 7
+
+
+def test_batch_gather_arguments(lib):
+    """ising_batch_gather refuses a null batch before touching the device."""
+    idx = (ctypes.c_int32 * 1)(0)
+    out = (ctypes.c_int64 * 3)()
+    assert lib.ising_batch_gather(None, 1, idx, out) == ising.ISING_EINVAL
+    assert list(out) == [0, 0, 0]

@@ -1,13 +1,15 @@
 """Host logic of the serving loop and the seeded workloads (CPU, no GPU).
 
 The server only schedules: it admits requests first come, first served while the
-batch has a slot and arena memory, runs quanta, and retires each lattice at its own
-sweep count.  Here the batch is a fake with the same calls and error codes (EBUSY
-when every slot is taken, ENOMEM when the arena is full), so the admission order,
-the blocked counters, the completion quanta and the memory returned are checked
-without a device.  The workload generators are checked against the recipes their
+batch has a slot and arena memory, keeps up to two quanta in flight, gathers the
+lattices that finish in a quantum behind it, and retires them once that quantum is
+seen to be done.  Here the batch is a fake with the same calls and error codes
+(EBUSY when every slot is taken, ENOMEM when the arena is full) whose work is done
+at once, so the admission order, the blocked counters, the quanta, the in-flight
+limit, the quantum sizes and the memory returned are checked without a device.  The workload generators are checked against the recipes their
 docstrings state.
 """
+import ctypes
 import math
 
 import numpy as np
@@ -26,7 +28,7 @@ class FakeBatch:
     def __init__(self, slots, max_L, budget, threads=0, stream=None):
         self.slots, self.max_L, self.budget = slots, max_L, budget
         self.live = {}
-        self.adds, self.runs, self.removed = [], [], []
+        self.adds, self.runs, self.removed, self.ops = [], [], [], []
         self.peak_bytes = 0
         FakeBatch.instances.append(self)
 
@@ -49,6 +51,7 @@ class FakeBatch:
     def run(self, n, graph_sweeps=0):
         assert graph_sweeps == n
         self.runs.append(sorted(v["seed"] for v in self.live.values()))
+        self.ops.append(("run", n))
         for v in self.live.values():
             v["done"] = min(v["sweeps"], v["done"] + n)
 
@@ -59,8 +62,17 @@ class FakeBatch:
         v = self.live[idx]
         return v["seed"], -v["sweeps"], v["done"]
 
+    def gather(self, idx, ptr):
+        """Writes (done, M = seed, E = -sweeps) of each slot into 3 int64 at ptr."""
+        out = (ctypes.c_int64 * (3 * len(idx))).from_address(ptr)
+        for k, i in enumerate(idx):
+            v = self.live[i]
+            out[3 * k], out[3 * k + 1], out[3 * k + 2] = v["done"], v["seed"], -v["sweeps"]
+        self.ops.append(("gather", tuple(idx)))
+
     def remove(self, idx):
         self.removed.append(self.live.pop(idx)["seed"])
+        self.ops.append(("remove", idx))
 
     def close(self):
         pass
@@ -77,17 +89,23 @@ def req(rid, arrival, L, sweeps):
     return Request(rid=rid, arrival=float(arrival), L=L, beta=0.44, seed=rid, sweeps=sweeps)
 
 
+def server(**kw):
+    return serve.Server(device_events=False, **kw)
+
+
 def test_first_come_first_served_with_slots(fake):
-    srv = serve.Server(hbm_budget_bytes=1 << 30, slots=2, max_L=1024, quantum=64)
+    srv = server(hbm_budget_bytes=1 << 30, slots=2, max_L=1024, quantum=64)
     reqs = [req(0, 0, 256, 64), req(1, 0, 512, 128), req(2, 0, 256, 64), req(3, 5, 128, 64)]
     results, st = srv.serve(reqs, realtime=False)
     b = fake.instances[0]
-    # quantum 0: r0, r1 in, r2 waits for a slot; r0 done.  Quantum 1: r2 in; r1 and r2
-    # done.  Nothing runs until r3 becomes visible at quantum 5.
-    assert b.runs == [[0, 1], [1, 2], [3]]
+    # r0, r1 in, r2 waits for a slot.  Quantum 1 finishes r0, quantum 2 (enqueued before
+    # quantum 1 is collected) r1; collecting quantum 1 frees r0's slot for r2, whose
+    # quantum 3 runs beside r1 until r1 is collected.  Nothing runs until r3 becomes
+    # visible after quantum 5.
+    assert b.runs == [[0, 1], [0, 1], [1, 2], [3]]
     assert b.adds == [0, 1, 2, 3] and sorted(b.removed) == [0, 1, 2, 3]
-    assert [r.rid for r in results] == [0, 2, 1, 3]
-    assert st.completed == 4 and st.quanta == 3 and st.max_active == 2
+    assert [r.rid for r in results] == [0, 1, 2, 3]
+    assert st.completed == 4 and st.quanta == 4 and st.max_active == 2
     assert st.admission_blocked_by_slots == 1 and st.admission_blocked_by_memory == 0
     assert st.flips == sum(r.L * r.L * r.sweeps for r in reqs)
     assert all((r.M, r.E) == (r.seed, -r.sweeps) for r in results)
@@ -96,7 +114,7 @@ def test_first_come_first_served_with_slots(fake):
 
 def test_memory_blocks_the_head_of_the_queue(fake):
     big, small = serve.Server.request_bytes(1024, 64), serve.Server.request_bytes(64, 64)
-    srv = serve.Server(hbm_budget_bytes=big + small, slots=8, max_L=1024, quantum=64)
+    srv = server(hbm_budget_bytes=big + small, slots=8, max_L=1024, quantum=64)
     reqs = [req(0, 0, 1024, 64), req(1, 0, 1024, 64), req(2, 0, 64, 64)]
     results, st = srv.serve(reqs, realtime=False)
     b = fake.instances[0]
@@ -109,12 +127,53 @@ def test_memory_blocks_the_head_of_the_queue(fake):
 
 
 def test_requests_that_can_never_fit_are_refused(fake):
-    srv = serve.Server(hbm_budget_bytes=serve.Server.request_bytes(512, 100), slots=4, max_L=512, quantum=64)
+    srv = server(hbm_budget_bytes=serve.Server.request_bytes(512, 100), slots=4, max_L=512, quantum=64)
     with pytest.raises(ValueError):
         srv.serve([req(0, 0, 1024, 10)], realtime=False)
-    srv = serve.Server(hbm_budget_bytes=1 << 20, slots=4, max_L=512, quantum=64)
+    srv = server(hbm_budget_bytes=1 << 20, slots=4, max_L=512, quantum=64)
     with pytest.raises(ValueError):
         srv.serve([req(0, 0, 256, 100_000)], realtime=False)
+
+
+def test_adaptive_quantum_follows_the_fewest_sweeps_left(fake):
+    """Quantum = the largest power of two in 8 .. 256 not above the fewest sweeps any
+    admitted lattice still has to be enqueued."""
+    srv = server(hbm_budget_bytes=1 << 30, slots=4, max_L=1024)
+    assert [srv.choose_quantum(n) for n in (1, 7, 8, 15, 16, 100, 256, 257, 10_000)] == \
+        [8, 8, 8, 8, 16, 64, 256, 256, 256]
+    results, st = srv.serve([req(0, 0, 256, 20), req(1, 0, 256, 1000)], realtime=False)
+    b = fake.instances[0]
+    sizes = [n for op, n in b.ops if op == "run"]
+    # 20 left -> 16, then 4 left -> 8 (r0 done), then r1 alone: 976 left -> 256 x 3, 208 -> 128, 80 -> 64, 16 -> 16
+    assert sizes == [16, 8, 256, 256, 256, 128, 64, 16]
+    assert sum(sizes) >= 1000 and [r.rid for r in results] == [0, 1]
+    assert fixed_sizes(fake, 32) == [32] * 32
+
+
+def fixed_sizes(fake, q):
+    srv = server(hbm_budget_bytes=1 << 30, slots=4, max_L=1024, quantum=q)
+    srv.serve([req(0, 0, 256, 1000)], realtime=False)
+    return [n for op, n in fake.instances[-1].ops if op == "run"]
+
+
+def test_at_most_two_quanta_in_flight(fake, monkeypatch):
+    """Each quantum's event reports done only on its second query: the server enqueues
+    two quanta, then collects before it enqueues a third."""
+    class Slow:
+        def __init__(self):
+            self.asked = 0
+
+        def query(self):
+            self.asked += 1
+            return self.asked > 1
+
+    srv = server(hbm_budget_bytes=1 << 30, slots=4, max_L=1024, quantum=8)
+    monkeypatch.setattr(srv, "_event", Slow)
+    results, st = srv.serve([req(k, 0, 128, 8 * (k + 1)) for k in range(3)], realtime=False)
+    ops = [op for op in fake.instances[0].ops if op[0] in ("run", "remove")]
+    # r0 (8 sweeps) finishes in quantum 1, r1 in quantum 2, r2 in quantum 3
+    assert ops == [("run", 8), ("run", 8), ("remove", 0), ("run", 8), ("remove", 1), ("remove", 2)]
+    assert [r.rid for r in results] == [0, 1, 2] and st.quanta == 3
 
 
 def test_request_bytes_and_percentiles():
