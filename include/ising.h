@@ -214,6 +214,15 @@ int ising_synchronize(ising_t h);
 int ising_set_specialize(int32_t mode);
 int ising_specialized(ising_t h, int32_t *specialized, char *note, int64_t len);
 
+/*
+ * Batches: while every lattice of a batch has the same thresholds, the batch sweeps
+ * with the multi-lattice kernel compiled for them (mode ALWAYS, or AUTO once the
+ * batch holds at least 16384^2 sites); a lattice of another temperature brings back
+ * the built-in kernel (captured graphs are re-captured).  *specialized = 1 while the
+ * compiled kernel is in use.  Host-only.  Errors: EINVAL (null argument).
+ */
+int ising_batch_specialized(ising_batch_t b, int32_t *specialized);
+
 /* Releases the handle and its device memory (NULL is a no-op).  Paper: none (resource
  * management of the Sec. 3 lattice). */
 int ising_free(ising_t h);
@@ -264,7 +273,8 @@ int ising_init3d(ising_t *out, int64_t L, double beta, uint64_t seed, int start,
  * simulations run as one replicated program, here one launch).
  * The lattices have no sweep limit: every ising_batch_run sweeps all of them, and
  * their (M, E) histories live outside the planes' arena and grow (doubling) when a
- * run needs room.  Built-in tile shapes, 256-thread CTAs, a stream the batch owns.
+ * run needs room.  Built-in tile shapes, 256-thread CTAs (512 when a side is at least
+ * 16,384), a stream the batch owns.
  * EINVAL, before any device work, for a null array, count outside 1 .. 2^20, or
  * any bad L, beta or start (the message names the lattice).  ENOMEM, ECUDA.
  */

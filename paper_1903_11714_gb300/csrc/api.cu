@@ -163,11 +163,14 @@ bool packed_L_ok(int64_t L)
 #ifndef ISING_TILE_WORDS
 #define ISING_TILE_WORDS 4096
 #endif
-int default_tile_rows(int64_t L)
+int default_tile_rows(int64_t L, int threads = 256)
 {
     const int64_t W = L / 64;
+    // lattices of 16,384 and more: 16 words per thread of the CTA (8,192 with 512
+    // threads), as for a single handle, so every warp has ~512 words of a tile
+    const int64_t words = L >= 16384 ? std::max<int64_t>(ISING_TILE_WORDS, 16 * threads) : ISING_TILE_WORDS;
     int tr = 64;
-    while (tr > 2 && ((int64_t)tr * W > ISING_TILE_WORDS || !tile_rows_ok(L, tr))) tr >>= 1;
+    while (tr > 2 && ((int64_t)tr * W > words || !tile_rows_ok(L, tr))) tr >>= 1;
     if (!tile_rows_ok(L, tr)) tr = 4;
     return tr;
 }
@@ -229,6 +232,9 @@ struct Engine {
     // single-lattice handles: the instance compiled for the lattice's thresholds (jit.cu),
     // used for the by-value launches; nullptr: the built-in instance
     const void* fixed = nullptr;
+    // batches: the multi-lattice instance compiled for the thresholds every lattice of the
+    // batch shares, or nullptr (the built-in instance)
+    const void* fixed_multi = nullptr;
     bool blocks = false;       // some lattice has column-block tiles (launch the build that handles them)
 
     void allow_blocks()
@@ -263,10 +269,10 @@ struct Engine {
         CK(packed_set_smem_limit(threads, smem));
         int per_sm = 0;
         CK(packed_occupancy(threads, smem, &per_sm, one_lattice));
-        if (fixed) {
-            // the grid follows the instance the plain launches use
+        if (fixed || fixed_multi) {
+            // the grid follows the instance the launches use
             int per_sm_fixed = 0;
-            CK(packed_fixed_configure(fixed, smem, threads, &per_sm_fixed));
+            CK(packed_fixed_configure(fixed ? fixed : fixed_multi, smem, threads, &per_sm_fixed));
             per_sm = per_sm_fixed;
         }
         if (per_sm < 1) return fail(ISING_EINVAL, "sweep kernel does not fit: %d threads, %zu B smem", threads, smem);
@@ -321,7 +327,7 @@ struct Engine {
             for (int c = 0; c < 2; ++c) {
                 cudaError_t e = launch_packed_half_sweep(tt, c, (int)k, d_status, grid, threads, stage_bytes, stream,
                                                          kWaitLimitCycles, 0u, by_value, blocks,
-                                                         by_value ? fixed : nullptr);
+                                                         by_value ? fixed : fixed_multi);
                 if (e != cudaSuccess) return cuda_fail(e, "packed half-sweep launch");
             }
         }
@@ -1177,6 +1183,36 @@ int ising_free(ising_t h)
 
 // ======================================================================= batch
 namespace {
+// A batch whose lattices all have one threshold pair sweeps with the multi-lattice
+// instance compiled for it (where the mode allows: always, or automatically once the
+// batch holds at least 16,384^2 sites); a lattice of another temperature, or a mode
+// that forbids it, brings back the built-in instance.  The kernel of captured graphs
+// changes with it, so they are dropped and the grid is sized for the new instance.
+int update_specialisation(ising_batch_t b)
+{
+    const int mode = g_specialize.load();
+    const LatticeDesc* first = nullptr;
+    bool same = true;
+    int64_t sites = 0;
+    for (const auto& s : b->slots) {
+        if (!s.used) continue;
+        sites += s.L * s.L;
+        if (!first)
+            first = &s.desc;
+        else if (s.desc.t2 != first->t2 || s.desc.t4 != first->t4 || s.desc.all2 != first->all2 ||
+                 s.desc.all4 != first->all4)
+            same = false;
+    }
+    const void* want = nullptr;
+    if (first && same && mode != ISING_SPECIALIZE_OFF &&
+        (mode == ISING_SPECIALIZE_ALWAYS || sites >= kSpecializeMinL * kSpecializeMinL))
+        want = jit_sweep_kernel(b->eng.threads, b->eng.blocks, first->t2, first->t4, first->all2, first->all4, nullptr,
+                                false);
+    if (want == b->eng.fixed_multi) return ISING_OK;
+    b->eng.fixed_multi = want;
+    return b->eng.configure();  // drops the graphs and sizes the grid
+}
+
 int rebuild_tiles(ising_batch_t b)
 {
     int32_t count = 0;
@@ -1188,7 +1224,9 @@ int rebuild_tiles(ising_batch_t b)
         ts[k + 1] = ts[k] + (s.used ? (int32_t)lattice_tiles(s.L, s.desc.tile_rows, s.desc.tile_words) : 0);
     }
     b->count = count;
-    return b->eng.upload_tiles(ts, count);
+    int rc = b->eng.upload_tiles(ts, count);
+    if (!rc) rc = update_specialisation(b);
+    return rc;
 }
 
 // Growable batches: before `sweeps` more sweeps, give every lattice's history room
@@ -1307,7 +1345,8 @@ int ising_batch_create(ising_batch_t* out, int32_t count, const int64_t* L, cons
         arena += FreeList::round_up((int64_t)sizeof(uint32_t) * 2 * L[k] * (L[k] / 64));
     }
     ising_batch_t b = nullptr;
-    int rc = ising_batch_create_ex(&b, count, max_L, arena, 0, nullptr);
+    // CTA size as for single handles: one 512-thread CTA per SM once a side reaches 16,384
+    int rc = ising_batch_create_ex(&b, count, max_L, arena, max_L >= 16384 ? 512 : 256, nullptr);
     if (rc) return rc;
     b->growable = true;
     constexpr int64_t kFirstHistory = 1024;  // sweeps of history at admission, doubled as needed
@@ -1338,7 +1377,7 @@ int ising_batch_add_tiled(ising_batch_t b, int64_t L, double beta, uint64_t seed
     const int W = (int)(L / 64);
     if (tile_words == 0) tile_words = default_tile_words(L);
     if (tile_words == W) {
-        if (tile_rows == 0 || !tile_rows_ok(L, tile_rows)) tile_rows = default_tile_rows(L);
+        if (tile_rows == 0 || !tile_rows_ok(L, tile_rows)) tile_rows = default_tile_rows(L, b->eng.threads);
     } else {
         if (tile_rows == 0) tile_rows = 2;
         if (!tile_ok(L, tile_rows, tile_words))
@@ -1457,6 +1496,13 @@ int ising_batch_progress(ising_batch_t b, int64_t* sweeps_done, int32_t n)
     int rc = b->eng.check_status();
     if (rc) return rc;
     for (int32_t k = 0; k < n; ++k) sweeps_done[k] = b->slots[k].used ? (int64_t)d[k].sweep : -1;
+    return ISING_OK;
+}
+
+int ising_batch_specialized(ising_batch_t b, int32_t* specialized)
+{
+    if (!b || !specialized) return fail(ISING_EINVAL, "null argument");
+    *specialized = b->eng.fixed_multi ? 1 : 0;
     return ISING_OK;
 }
 

@@ -12,9 +12,9 @@ namespace ising {
 // one != nullptr: a launch over that single lattice, whose descriptor (with the
 // sweep index the host knows) is passed by value; tt is then not read.  Not for
 // graph capture, since the sweep index is baked into the launch.  blocks: some
-// lattice of tt may have column-block tiles (tile_words < W).  fixed (with one):
-// that lattice's instance compiled for its thresholds (jit_sweep_kernel), launched
-// instead of the built-in one.
+// lattice of tt may have column-block tiles (tile_words < W).  fixed: an instance
+// compiled for the thresholds (jit_sweep_kernel) of that lattice (with one) or of
+// every lattice of tt (without), launched instead of the built-in one.
 cudaError_t launch_packed_half_sweep(const TileTable& tt, int colour, int step, int* status, int grid,
                                      int threads, int smem_stage_bytes, cudaStream_t s,
                                      long long wait_limit = kWaitLimitCycles, uint32_t extra_tx = 0,

@@ -14,7 +14,9 @@ namespace ising {
 // and cached.  Returns nullptr, with the reason in *why, when NVRTC cannot be
 // loaded, the compile or load fails, or specialisation is switched off.
 const void* jit_sweep_kernel(int threads, bool blocks, uint32_t t2, uint32_t t4, uint32_t all2, uint32_t all4,
-                             std::string* why);
+                             std::string* why, bool one = true);
+// one = false: the multi-lattice instance (descriptors read from the tile table; for a
+// batch whose lattices all have these thresholds; blocks: it may hold column blocks).
 
 // Process-wide switch (default on); off makes jit_sweep_kernel return nullptr.
 void jit_set_enabled(bool on);

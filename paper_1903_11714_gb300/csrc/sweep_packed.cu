@@ -53,11 +53,11 @@ cudaError_t launch_packed_half_sweep(const TileTable& tt, int colour, int step, 
 {
     int stage_words = smem_stage_bytes / 4;
     const size_t smem = (size_t)packed_smem_header_bytes(threads) + 2 * (size_t)smem_stage_bytes;
-    if (one && fixed) {
-        // the single-lattice instance compiled for this lattice's thresholds (jit.cu):
-        // the same parameters as the built-in instance
+    if (fixed) {
+        // an instance compiled for the thresholds of this lattice (one) or of every lattice
+        // of the table (jit.cu): the same parameters as the built-in instances
         TileTable t = tt;
-        LatticeDesc d = *one;
+        LatticeDesc d = one ? *one : LatticeDesc{};
         void* args[] = {&t, &d, &colour, &step, &status, &stage_words, &wait_limit, &extra_tx};
         return cudaLaunchKernel(fixed, dim3(grid), dim3(threads), args, smem, s);
     }

@@ -65,6 +65,7 @@ _SIGS = {
     "ising_batch_progress": (ctypes.c_int, [_vp, _P(_i64), _i32]),
     "ising_batch_observables": (ctypes.c_int, [_vp, _i32, _P(_i64), _P(_i64)]),
     "ising_batch_gather": (ctypes.c_int, [_vp, _i32, _P(_i32), _vp]),
+    "ising_batch_specialized": (ctypes.c_int, [_vp, _P(_i32)]),
     "ising_batch_observables_ex": (ctypes.c_int, [_vp, _i32, _P(_i64), _P(_i64), _P(_i64)]),
     "ising_batch_history": (ctypes.c_int, [_vp, _i32, _i64, _i64, _P(_i64), _P(_i64)]),
     "ising_batch_moments": (ctypes.c_int, [_vp, _i32, _i64, _P(_d), _P(_u64)]),
@@ -483,6 +484,12 @@ class Batch:
         out = np.empty((L, L), dtype=np.int8)
         _check(lib().ising_batch_get_lattice(self.b, int(idx), _ptr(out, ctypes.c_int8)))
         return out
+
+    def specialized(self) -> bool:
+        """True while the batch sweeps with a kernel compiled for its one temperature."""
+        flag = ctypes.c_int32()
+        _check(lib().ising_batch_specialized(self.b, ctypes.byref(flag)))
+        return bool(flag.value)
 
     def gather(self, idx, out_ptr: int) -> None:
         """Enqueue (sweeps done, M, E) of slots idx into out_ptr (3 int64 each,

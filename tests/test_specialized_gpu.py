@@ -95,3 +95,40 @@ def test_large_single_handles_take_512_thread_ctas_and_stay_exact():
         assert np.array_equal(lat.get_lattice(), ref), mode
         lat.close()
     ising.ising_set_specialize(ising.SPECIALIZE_AUTO)
+
+
+def test_batch_of_one_temperature_specialises_until_another_joins():
+    """Three lattices at one beta sweep with the multi-lattice kernel compiled for it;
+    a fourth at another beta brings back the built-in kernel mid-run (graphs
+    re-captured).  Every chain equals the oracle's."""
+    ising.ising_set_specialize(ising.SPECIALIZE_ALWAYS)
+    beta, other = 0.4406868, 0.31
+    specs = [(256, 51, ising.HOT), (320, 52, ising.COLD), (512, 53, ising.HOT)]
+    b = ising.Batch(4, 512, 8 << 20, 0)
+    idx = [b.add(L, beta, seed, start, 12) for L, seed, start in specs]
+    assert b.specialized()
+    b.run(6, graph_sweeps=3)
+    j = b.add(384, other, 54, ising.HOT, 12)
+    assert not b.specialized()
+    b.run(6, graph_sweeps=3)
+    b.synchronize()
+    for (L, seed, start), i in zip(specs, idx):
+        ref, Mr, Er, _ = oracle.run(L, beta, seed, start, 12)
+        M, E = b.history(i)
+        assert np.array_equal(M, Mr) and np.array_equal(E, Er), L
+        assert np.array_equal(b.get_lattice(i), ref), L
+    ref, Mr, Er, _ = oracle.run(384, other, 54, ising.HOT, 6)
+    M, E = b.history(j)
+    assert np.array_equal(M, Mr) and np.array_equal(E, Er)
+    assert np.array_equal(b.get_lattice(j), ref)
+    b.remove(j)
+    assert b.specialized()  # one temperature again
+    b.close()
+    ising.ising_set_specialize(ising.SPECIALIZE_AUTO)
+
+
+def test_automatic_mode_leaves_small_batches_built_in():
+    ising.ising_set_specialize(ising.SPECIALIZE_AUTO)
+    b = ising.Batch.from_arrays([1024] * 4, [0.44] * 4, [1, 2, 3, 4], [ising.HOT] * 4)
+    assert not b.specialized()
+    b.close()
