@@ -448,6 +448,7 @@ struct ising_s {
     double* d_mom = nullptr;    // 6 doubles
     uint64_t* d_sums = nullptr; // 11 limbs
     std::string kernel_note;    // which sweep kernel runs, and why (ising_specialized)
+    const void* cubic_fixed[2] = {nullptr, nullptr};  // 3D: the colours' compiled instances
 };
 
 struct ising_batch_s {
@@ -797,7 +798,7 @@ int ising_specialized(ising_t h, int32_t* specialized, char* note, int64_t len)
 {
     int rc = check_handle(h);
     if (rc) return rc;
-    if (specialized) *specialized = h->eng.fixed ? 1 : 0;
+    if (specialized) *specialized = (h->eng.fixed || h->cubic_fixed[0]) ? 1 : 0;
     if (note && len > 0) {
         const std::string& n = h->kernel_note.empty() ? std::string("built-in") : h->kernel_note;
         const size_t k = std::min<size_t>(n.size(), (size_t)len - 1);
@@ -840,6 +841,25 @@ int ising_init3d(ising_t* out, int64_t L, double beta, uint64_t seed, int start,
     if (rc) {
         delete h;
         return rc;
+    }
+    // the sweep kernel: compiled for this lattice's thresholds where the mode asks for it
+    // (automatic: at least 16384^2 sites) and it can be had, else the built-in one
+    const int mode = g_specialize.load();
+    if (mode == ISING_SPECIALIZE_OFF) {
+        h->kernel_note = "built-in: specialisation switched off";
+    } else if (mode == ISING_SPECIALIZE_AUTO && L * L * L < kSpecializeMinL * kSpecializeMinL) {
+        h->kernel_note = "built-in: fewer than 16384^2 sites (automatic mode)";
+    } else {
+        uint32_t t[3], all[3];
+        for (int k = 0; k < 3; ++k) {
+            t[k] = thr32(T[k]);
+            all[k] = all32(T[k]);
+        }
+        std::string why;
+        if (jit_cubic_kernels(kCubicThreads, cubic_words_per_group(L), t, all, h->cubic_fixed, &why))
+            h->kernel_note = "specialised: compiled for this lattice's thresholds";
+        else
+            h->kernel_note = "built-in: " + why;
     }
     cudaError_t e = cudaMalloc(&h->d_me0, 2 * sizeof(int64_t));
     if (e == cudaSuccess) e = cudaMalloc(&h->d_mom, 6 * sizeof(double));
@@ -886,7 +906,8 @@ int ising_sweep(ising_t h, int64_t n)
         const CubicDesc d = cubic_desc(h);
         for (int64_t k = 0; k < n; ++k)
             for (int c = 0; c < 2; ++c) {
-                cudaError_t e = launch_cubic_half_sweep(d, c, (uint32_t)(h->sweeps_done + k), h->stream);
+                cudaError_t e = launch_cubic_half_sweep(d, c, (uint32_t)(h->sweeps_done + k), h->stream,
+                                                        h->cubic_fixed[0] ? h->cubic_fixed : nullptr);
                 if (e != cudaSuccess) return cuda_fail(e, "3D half-sweep launch");
             }
     } else {

@@ -73,4 +73,20 @@ constexpr int64_t kStageCapBytes = 100 * 1024;
 // its CTAs return.
 constexpr long long kWaitLimitCycles = 4000000000LL;
 
+// One cubic lattice of a half-sweep launch (passed by value).
+struct CubicDesc {
+    uint32_t* plane[2];        // [0] black, [1] white; each L*L*W words
+    int64_t* hist;             // (M, E) pairs indexed by sweep number
+    uint64_t key;              // Philox key (seed)
+    int32_t L, W;              // side, words per plane row (L / 64)
+    uint32_t t2, t4, t6;       // thresholds min(T, 2^32 - 1) for h = 2, 4, 6
+    uint32_t all2, all4, all6; // ~0u when the threshold is 2^32
+};
+
+constexpr int64_t kCubicMaxL = 8192;
+
+// Cubic sides whose Philox call index q = 8 (p >> 5) stays below 2^32 (so the
+// per-launch Philox constants hold for every word).
+__host__ __device__ inline bool cubic_q_small(int64_t L) { return (uint64_t)L * L * L <= (1ull << 35); }
+
 }  // namespace ising

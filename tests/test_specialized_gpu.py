@@ -132,3 +132,22 @@ def test_automatic_mode_leaves_small_batches_built_in():
     b = ising.Batch.from_arrays([1024] * 4, [0.44] * 4, [1, 2, 3, 4], [ising.HOT] * 4)
     assert not b.specialized()
     b.close()
+
+
+@pytest.mark.parametrize("L,beta,seed,sweeps", [(64, 0.2216546, 61, 5),    # one word per row: one-word groups
+                                                 (256, 0.2216546, 62, 3),   # four-word groups
+                                                 (128, 0.0, 63, 2),         # T = 2^32: every site flips
+                                                 (192, 200.0, 64, 3)])      # T = 0: only h <= 0 flips
+def test_cubic_specialised_kernel_matches_oracle(L, beta, seed, sweeps):
+    """The 3D sweep compiled for its three thresholds gives the oracle's cube and M, E."""
+    ising.ising_set_specialize(ising.SPECIALIZE_ALWAYS)
+    ref, Mr, Er, _ = oracle.run3d((L, L, L), beta, seed, oracle.HOT, sweeps)
+    lat = ising.Lattice3D(L, beta, seed, ising.HOT)
+    spec, note = lat.specialized()
+    assert spec, note
+    lat.sweep(sweeps)
+    M, E = lat.history()
+    assert np.array_equal(M, Mr) and np.array_equal(E, Er)
+    assert np.array_equal(lat.get_lattice(), ref)
+    lat.close()
+    ising.ising_set_specialize(ising.SPECIALIZE_AUTO)
