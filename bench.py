@@ -48,7 +48,7 @@ N_SMS = 152
 KERNEL_SOURCES = {
     "packed_half_sweep": ("sweep_packed_kernel.cuh", "word_update.cuh", "philox.cuh", "ising_device.cuh",
                           "jit.cu"),
-    "cubic_half_sweep": ("sweep3d.cu", "sweep3d.cuh", "word_update.cuh", "philox.cuh", "ising_device.cuh"),
+    "cubic_half_sweep": ("sweep3d_kernel.cuh", "word_update.cuh", "philox.cuh", "ising_device.cuh", "jit.cu"),
 }
 # algorithmic bytes per site per sweep (packed): each half-sweep reads the target
 # and source planes and writes the target plane, N/2 bits each
