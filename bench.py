@@ -49,10 +49,13 @@ KERNEL_SOURCES = {
     "packed_half_sweep": ("sweep_packed_kernel.cuh", "word_update.cuh", "philox.cuh", "ising_device.cuh",
                           "jit.cu"),
     "cubic_half_sweep": ("sweep3d_kernel.cuh", "word_update.cuh", "philox.cuh", "ising_device.cuh", "jit.cu"),
+    "int8_half_sweep": ("sweep_int8.cu", "word_update.cuh", "philox.cuh", "ising_device.cuh"),
 }
 # algorithmic bytes per site per sweep (packed): each half-sweep reads the target
 # and source planes and writes the target plane, N/2 bits each
 BYTES_PER_SITE_SWEEP = 3.0 * 2 * (0.5 / 8.0)
+# int8: each half-sweep reads and writes all N bytes for N/2 updated sites
+INT8_BYTES_PER_SITE = 4.0
 
 
 def max_over_ranks(value: float, dist, device: str) -> float:
@@ -188,7 +191,8 @@ PIPE_NAMES = {"alu": "ALU pipe (logic, shifts, compares)",
               "fmaheavy": "FMA-heavy pipe (integer multiplies: the Philox products)"}
 
 
-def kernel_roofline(kernel: str, sites_per_launch: float, t_launch_s: float, sm_max: float, peaks: dict) -> dict:
+def kernel_roofline(kernel: str, sites_per_launch: float, t_launch_s: float, sm_max: float, peaks: dict,
+                    bytes_per_site: float = BYTES_PER_SITE_SWEEP) -> dict:
     """Roofline of one half-sweep launch.  The sweep is integer work on two pipes of 16
     lanes per scheduler (4 per SM): the ALU pipe (the Philox XORs, the bit-plane
     comparison, the neighbour adder) and the FMA-heavy pipe (the Philox 32x32->64
@@ -203,7 +207,7 @@ def kernel_roofline(kernel: str, sites_per_launch: float, t_launch_s: float, sm_
     c = committed_counters(kernel)
     alu_peak = ALU_OPS_PER_CLK_SM * N_SMS * sm_max * 1e6 / 1e12
     issue_peak = ISSUE_SLOTS_PER_CLK_SM * N_SMS * sm_max * 1e6 / 1e12
-    hbm_bytes = BYTES_PER_SITE_SWEEP * sites_per_launch
+    hbm_bytes = bytes_per_site * sites_per_launch
     out = {"bound": "alu", "achieved": None, "peak": alu_peak, "unit": "Tops/s", "frac": None, "traffic": None,
            "peak_basis": f"4 schedulers x 16 lanes = {ALU_OPS_PER_CLK_SM:.0f} lane-operations/clk/SM per integer "
                          f"pipe x {N_SMS} SMs x {sm_max:.0f} MHz (the probe in this line measures the lanes per "
@@ -698,9 +702,8 @@ def main() -> None:
     if kernel == ising.PACKED:
         roofline = kernel_roofline("packed_half_sweep", N / 2, t_launch_s, sm_max, peaks)
     else:
-        roofline = {"bound": "alu", "achieved": None, "peak": None, "unit": "Tinst/s", "frac": None, "traffic": None,
-                    "hbm_achieved_gbs": 2.0 * N / t_launch_s / 1e9, "hbm_peak_gbs": peaks.get("hbm_gbs", 6800.0),
-                    "note": "plain int8 kernel: no committed counters"}
+        # the int8 kernel reads and writes every byte of the lattice per half-sweep
+        roofline = kernel_roofline("int8_half_sweep", N / 2, t_launch_s, sm_max, peaks, bytes_per_site=INT8_BYTES_PER_SITE)
     roofline["probe_alu_ops_per_clk_sm"] = alu_per_clk
     roofline["probe_mul_xor_steps_per_clk_sm"] = mul_per_clk
 
@@ -784,9 +787,11 @@ def run_plain_int8(cfg, steps: int, warmup: int) -> dict:
     ms = e0.elapsed_time(e1)
     lat.close()
     N = cfg.L * cfg.L
+    peaks = measured_peaks()
+    roof = kernel_roofline("int8_half_sweep", N / 2, ms * 1e-3 / (2 * steps), float(peaks.get("sm_max_mhz", 2070.0)),
+                           peaks, bytes_per_site=INT8_BYTES_PER_SITE)
     return {"metric": "spin-flip attempts/ns, plain int8 kernel", "workload": "single_large", "unit": UNIT,
-            "value": steps * N / (ms * 1e6), "steps": steps, "basis": "CUDA events",
-            "hbm_achieved_gbs": 4.0 * N * steps / (ms * 1e-3) / 1e9,
+            "value": steps * N / (ms * 1e6), "steps": steps, "basis": "CUDA events", "roofline": roof,
             "note": "row-major int8 lattice (4.3 GB), each half-sweep reads and writes every byte"}
 
 
