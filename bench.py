@@ -50,6 +50,8 @@ KERNEL_SOURCES = {
                           "jit.cu"),
     "cubic_half_sweep": ("sweep3d_kernel.cuh", "word_update.cuh", "philox.cuh", "ising_device.cuh", "jit.cu"),
     "int8_half_sweep": ("sweep_int8.cu", "word_update.cuh", "philox.cuh", "ising_device.cuh"),
+    "cluster_sweep": ("sweep_cluster.cu", "sweep_packed_kernel.cuh", "word_update.cuh", "philox.cuh",
+                      "ising_device.cuh"),
 }
 # algorithmic bytes per site per sweep (packed): each half-sweep reads the target
 # and source planes and writes the target plane, N/2 bits each
@@ -335,8 +337,10 @@ def run_single_small(args) -> dict:
 
 
 def run_batched(args, which: str) -> dict:
-    """Batched forms (one persistent launch per half-sweep over all lattices)
-    against plain launches of the int8 and packed kernels, one lattice at a time."""
+    """Batched forms (one persistent launch per half-sweep over all lattices, or, for
+    lattices of one side L <= 4096, each resident in a thread-block cluster for up to
+    4,096 sweeps per launch) against plain launches of the int8 and packed kernels, one
+    lattice at a time."""
     import torch
 
     from paper_1903_11714_gb300 import ising, workloads
@@ -364,23 +368,45 @@ def run_batched(args, which: str) -> dict:
             tiles[L], tuned_threads[L], _ = ising.ising_autotune(L)
     work = {L: sum(l.L * l.L for l in lats if l.L == L) for L in tiles}
     threads = tuned_threads[max(work, key=work.get)]
-    b = ising.Batch(len(lats), max_L, arena, threads, stream=st)
-    for l in lats:
-        b.add(l.L, l.beta, l.seed, l.start, l.sweeps + warm, tiles.get(l.L, 0))
-    b.run(warm, graph_sweeps=graph)
-    b.synchronize()
-    e0, e1 = _events(torch, st)
-    torch.cuda.nvtx.range_push("timed")  # lets a profiler pick this region's launches
-    e0.record(st)
-    b.run(sweeps, graph_sweeps=graph)
-    e1.record(st)
-    torch.cuda.synchronize()
-    torch.cuda.nvtx.range_pop()
-    b.synchronize()
-    ms = e0.elapsed_time(e1)
+    modes = {"auto": ising.CLUSTER_AUTO, "off": ising.CLUSTER_OFF, "always": ising.CLUSTER_ALWAYS}
+
+    def timed(mode: int, nvtx: bool):
+        b = ising.Batch(len(lats), max_L, arena, threads, stream=st)
+        b.set_cluster(mode)
+        for l in lats:
+            b.add(l.L, l.beta, l.seed, l.start, l.sweeps + warm, tiles.get(l.L, 0))
+        b.run(warm, graph_sweeps=graph)
+        b.synchronize()
+        e0, e1 = _events(torch, st)
+        if nvtx:
+            torch.cuda.nvtx.range_push("timed")  # lets a profiler pick this region's launches
+        e0.record(st)
+        b.run(sweeps, graph_sweeps=graph)
+        e1.record(st)
+        torch.cuda.synchronize()
+        if nvtx:
+            torch.cuda.nvtx.range_pop()
+        b.synchronize()
+        cluster = b.cluster_size()
+        b.close()
+        return e0.elapsed_time(e1), cluster
+
+    ms, cluster = timed(modes[args.batch_cluster], True)
     flips = sweeps * sum(l.L * l.L for l in lats)
     batched = flips / (ms * 1e6)
-    b.close()
+    tiled = roofline = None
+    if cluster:
+        # the cluster kernel's roofline over the timed launches (up to 4,096 sweeps each):
+        # its busier pipe against the whole GPU's; HBM carries only each launch's load and
+        # store of the planes and the (M, E) pairs
+        launches = -(-sweeps // 4096)
+        peaks = measured_peaks()
+        plane_bytes = 2 * sum(l.L * l.L // 8 for l in lats) + 16 * len(lats) * sweeps / launches
+        roofline = kernel_roofline("cluster_sweep", flips / launches, ms * 1e-3 / launches,
+                                   float(peaks.get("sm_max_mhz", 2070.0)), peaks,
+                                   bytes_per_site=plane_bytes / (flips / launches))
+        # the same batch on the tiled kernel, for comparison
+        tiled = flips / (timed(ising.CLUSTER_OFF, False)[0] * 1e6)
     # plain: each lattice alone, its own launches, for a shorter run (same per-sweep work)
     plain = {}
     n_plain = min(sweeps, 100)
@@ -402,9 +428,12 @@ def run_batched(args, which: str) -> dict:
             "unit": UNIT, "value": batched, "plain_int8_value": plain["int8"],
             "plain_packed_value": plain["packed"], "lattices": len(lats), "sweeps": sweeps,
             "graph_sweeps": graph, "ms": ms, "basis": "CUDA events on the batch's stream",
-            "tile_rows_by_L": tiles or None, "threads": threads,
-            "note": f"batched = one persistent launch per half-sweep over all lattices, a CUDA graph of {graph} "
-                    f"sweeps replayed; plain = each lattice alone with its own launches, {n_plain} sweeps each"}
+            "tile_rows_by_L": tiles or None, "threads": threads, "cluster_size": cluster,
+            "tiled_value": tiled, "roofline": roofline,
+            "note": (f"batched = every lattice resident in the shared memory of a cluster of {cluster} CTAs, "
+                     "up to 4,096 sweeps per launch" if cluster else
+                     f"batched = one persistent launch per half-sweep over all lattices, a CUDA graph of {graph} "
+                     "sweeps replayed") + f"; plain = each lattice alone with its own launches, {n_plain} sweeps each"}
 
 
 def run_cubic(args) -> None:
@@ -619,6 +648,8 @@ def make_parser() -> argparse.ArgumentParser:
     ap.add_argument("--batch-tile-rows", type=int, default=0,
                     help="scan / uneven: tile rows for every side instead of the autotuner's (with --batch-threads)")
     ap.add_argument("--batch-threads", type=int, default=0, help="scan / uneven: CTA size instead of the autotuner's")
+    ap.add_argument("--batch-cluster", choices=["auto", "off", "always"], default="auto",
+                    help="scan / uneven: cluster-resident form of one-side batches (ising_batch_set_cluster)")
     ap.add_argument("--no-sub", action="store_true",
                     help="default run: skip the repeats and the records of configurations 1, 3, 4, 5 and int8")
     ap.add_argument("--repeats", type=int, default=5, help="extra timings of the K timed steps (spread)")

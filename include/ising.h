@@ -223,6 +223,31 @@ int ising_specialized(ising_t h, int32_t *specialized, char *note, int64_t len);
  */
 int ising_batch_specialized(ising_batch_t b, int32_t *specialized);
 
+/*
+ * Cluster-resident batches.  While every lattice of a batch has the same side
+ * L <= 4096 (whole-row tiles), the batch can keep each lattice in the shared
+ * memory of one thread-block cluster for a whole run (CTA r of a cluster of C
+ * holds rows [r L/C, (r+1) L/C), reading its halo rows from the neighbouring CTAs'
+ * shared memory after every half-sweep) and run up to 4,096 sweeps per launch; C
+ * is the largest power of two (at most 16, at least 16 rows per CTA) for which
+ * every lattice's cluster can be resident at once (else 1, the lattices then
+ * running in waves).  The chain is the tiled kernel's, bit for bit.
+ * mode ISING_CLUSTER_OFF keeps the batch on the tiled kernel; ISING_CLUSTER_AUTO
+ * (the default) takes the cluster form when its estimated rate (about 22 sites/ns
+ * per SM its CTAs occupy) beats the tiled kernel's (about 25.7 sites/ns per SM,
+ * halved at 5e7 sites per sweep): many small lattices, or a few of L <= 2048;
+ * ISING_CLUSTER_ALWAYS whenever the lattices fit.
+ * ising_batch_cluster_size gives the C in use (0: the tiled kernel).  Host-only;
+ * the mode is re-applied whenever lattices are added or removed.
+ * Paper: Sec. 3.1 (the schedule), Sec. 4.1 (scans of small lattices).
+ * Errors: EINVAL (null argument, mode not 0-2).
+ */
+#define ISING_CLUSTER_OFF 0
+#define ISING_CLUSTER_AUTO 1
+#define ISING_CLUSTER_ALWAYS 2
+int ising_batch_set_cluster(ising_batch_t b, int32_t mode);
+int ising_batch_cluster_size(ising_batch_t b, int32_t *cluster_size);
+
 /* Releases the handle and its device memory (NULL is a no-op).  Paper: none (resource
  * management of the Sec. 3 lattice). */
 int ising_free(ising_t h);

@@ -235,6 +235,11 @@ struct Engine {
     // batches: the multi-lattice instance compiled for the thresholds every lattice of the
     // batch shares, or nullptr (the built-in instance)
     const void* fixed_multi = nullptr;
+    // batches of lattices of one side L <= 4096: CTAs per cluster of the cluster-resident
+    // sweep (0: the tiled kernel), the side and the table's lattice count
+    ClusterPlan cluster;
+    int64_t cluster_L = 0;
+    int cluster_count = 0;
     bool blocks = false;       // some lattice has column-block tiles (launch the build that handles them)
 
     void allow_blocks()
@@ -339,6 +344,18 @@ struct Engine {
     int run(int64_t sweeps, int graph_sweeps)
     {
         if (sweeps == 0) return ISING_OK;
+        if (cluster.C > 0) {
+            // every lattice stays in its cluster's shared memory for up to 4,096 sweeps per
+            // launch; no graph is needed
+            for (int64_t done = 0; done < sweeps;) {
+                const int chunk = (int)std::min<int64_t>(sweeps - done, 4096);
+                CK(launch_cluster_sweeps(d_desc, cluster_count, cluster_L, cluster, chunk, stream));
+                cudaError_t e = launch_packed_advance(d_desc, d_count, max_count, chunk, stream);
+                if (e != cudaSuccess) return cuda_fail(e, "advance launch");
+                done += chunk;
+            }
+            return ISING_OK;
+        }
         if (graph_sweeps <= 0) return enqueue_sweeps(sweeps);
         if (sweeps % graph_sweeps) return fail(ISING_EINVAL, "sweeps %lld not a multiple of graph_sweeps %d",
                                                (long long)sweeps, graph_sweeps);
@@ -464,6 +481,7 @@ struct ising_batch_s {
     // growable (made from arrays): lattices have no sweep limit, their histories are
     // allocated apart from the arena and doubled when a run needs more room
     bool growable = false;
+    int cluster_mode = ISING_CLUSTER_AUTO;  // ising_batch_set_cluster
     int capacity = 0;
     int64_t max_L = 0;
     cudaStream_t stream = nullptr;
@@ -1234,6 +1252,40 @@ int update_specialisation(ising_batch_t b)
     return b->eng.configure();  // drops the graphs and sizes the grid
 }
 
+// Lattices of one side L <= 4096 with whole-row tiles are swept by the cluster-resident
+// kernel (one thread-block cluster per lattice, all of a run's sweeps in one launch)
+// when a cluster plan exists and (in the automatic mode) its estimated rate beats the
+// tiled kernel's; otherwise, or when switched off, by the tiled kernel, which spreads
+// a few lattices over every SM.  Estimates (GB300 measurements): the cluster form
+// sweeps about 22 sites/ns per SM its CTAs occupy (a 512-thread CTA a whole SM, a
+// 256-thread one half); the tiled kernel about 25.7 sites/ns per SM at large sizes,
+// half of that at 5e7 sites per sweep, below which launch latency dominates.
+int update_cluster(ising_batch_t b)
+{
+    int64_t L = 0;
+    bool one_side = true;
+    for (const auto& s : b->slots) {
+        if (!s.used) continue;
+        if (L == 0) L = s.L;
+        if (s.L != L || s.desc.tile_words != s.desc.W) one_side = false;
+    }
+    ClusterPlan p;
+    if (b->cluster_mode != ISING_CLUSTER_OFF && L > 0 && one_side && L <= cluster_max_L()) {
+        p = cluster_plan(L, b->count);
+        if (b->cluster_mode == ISING_CLUSTER_AUTO && p.C > 0) {
+            int live = 0;
+            for (const auto& s : b->slots) live += s.used && s.desc.active ? 1 : 0;
+            const double sms = sm_count(), sites = (double)L * (double)L * live;
+            const double used = std::min(sms, (double)b->count * p.C * p.threads / 512.0);
+            if (22.0 * used < 25.7 * sms * sites / (sites + 5e7)) p = ClusterPlan();
+        }
+    }
+    b->eng.cluster = p;
+    b->eng.cluster_L = L;
+    b->eng.cluster_count = b->count;
+    return ISING_OK;
+}
+
 int rebuild_tiles(ising_batch_t b)
 {
     int32_t count = 0;
@@ -1247,6 +1299,7 @@ int rebuild_tiles(ising_batch_t b)
     b->count = count;
     int rc = b->eng.upload_tiles(ts, count);
     if (!rc) rc = update_specialisation(b);
+    if (!rc) rc = update_cluster(b);
     return rc;
 }
 
@@ -1520,6 +1573,22 @@ int ising_batch_progress(ising_batch_t b, int64_t* sweeps_done, int32_t n)
     return ISING_OK;
 }
 
+int ising_batch_set_cluster(ising_batch_t b, int32_t mode)
+{
+    if (!b) return fail(ISING_EINVAL, "null batch");
+    if (mode != ISING_CLUSTER_OFF && mode != ISING_CLUSTER_AUTO && mode != ISING_CLUSTER_ALWAYS)
+        return fail(ISING_EINVAL, "cluster mode %d is not 0, 1 or 2", mode);
+    b->cluster_mode = mode;
+    return update_cluster(b);
+}
+
+int ising_batch_cluster_size(ising_batch_t b, int32_t* cluster_size)
+{
+    if (!b || !cluster_size) return fail(ISING_EINVAL, "null argument");
+    *cluster_size = b->eng.cluster.C;
+    return ISING_OK;
+}
+
 int ising_batch_specialized(ising_batch_t b, int32_t* specialized)
 {
     if (!b || !specialized) return fail(ISING_EINVAL, "null argument");
@@ -1676,6 +1745,7 @@ int ising_autotune(int64_t L, int32_t* tile_rows, int32_t* threads, double* ms)
         const int64_t per = (int64_t)sizeof(uint32_t) * 2 * L * (L / 64) + 16 * (2 * reps + 4) + 512;
         int rc = ising_batch_create_ex(&b, copies, L, per * copies + 4096, thread_opts[ti], nullptr);
         if (rc) return rc;
+        b->cluster_mode = ISING_CLUSTER_OFF;  // the tiled kernel's shapes are what is timed
         for (int tr = 2; tr <= kMaxTileRows; tr *= 2) {
             if (!tile_rows_ok(L, tr)) continue;  // whole rows only
             std::vector<int32_t> idx((size_t)copies, -1);

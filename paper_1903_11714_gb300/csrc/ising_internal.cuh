@@ -29,6 +29,20 @@ int packed_resident_max_L();
 cudaError_t launch_packed_resident(const LatticeDesc& d, int nsweeps, cudaStream_t s);
 cudaError_t launch_packed_advance(LatticeDesc* desc, const int32_t* count, int max_count, int steps,
                                   cudaStream_t s);
+// Cluster-resident sweeps (sweep_cluster.cu): lattices of one side L <= cluster_max_L()
+// kept in the shared memory of one thread-block cluster of C CTAs each (threads per
+// CTA, dynamic shared memory per CTA).  cluster_plan gives the plan for `count`
+// lattices (C = 0: none fits); the launch runs nsweeps sweeps of every live lattice of
+// desc[0..count), each stopping at its limit.
+struct ClusterPlan {
+    int C = 0;
+    int threads = 0;
+    size_t smem = 0;
+};
+int cluster_max_L();
+ClusterPlan cluster_plan(int64_t L, int count);
+cudaError_t launch_cluster_sweeps(const LatticeDesc* desc, int count, int64_t L, const ClusterPlan& p, int nsweeps,
+                                  cudaStream_t s);
 // Parameter blocks of the by-value updates (each under the 4 KB kernel-parameter limit).
 struct TileChunk {
     static constexpr int kMax = 960;

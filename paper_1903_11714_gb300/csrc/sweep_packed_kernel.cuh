@@ -354,7 +354,7 @@ __device__ __forceinline__ void drain_queue(const TileCtx& x, const PhiloxWordCo
 //
 // BLOCKS: the tile is a column block (its source rows carry halo words, so the
 // horizontal neighbours need no wrap); else whole rows (CW = SW = W, wrapped).
-template <int NT, int G, bool COUNT, bool BLOCKS, typename TH>
+template <int NT, int G, bool COUNT, bool BLOCKS, typename TH, bool INPLACE = false>
 __device__ __forceinline__ void update_tile(const TileCtx& x, const PhiloxWordConsts& pc_tile, int nwords, uint4* wq,
                                             uint32_t& ups, uint32_t& anti)
 {
@@ -418,7 +418,14 @@ __device__ __forceinline__ void update_tile(const TileCtx& x, const PhiloxWordCo
 #pragma unroll
             for (int k = 0; k < G; ++k) nw[k] = tg[k] ^ fm[k];
         }
-        if (valid) store_group<G>(x.out + pos0, nw);
+        if constexpr (INPLACE) {
+            uint32_t st[G];
+#pragma unroll
+            for (int k = 0; k < G; ++k) st[k] = und[k] != 0u ? nw[k] ^ fm[k] : nw[k];  // queued: the old word
+            if (valid) store_group<G>(x.out + pos0, st);
+        } else {
+            if (valid) store_group<G>(x.out + pos0, nw);
+        }
 #pragma unroll
         for (int k = 0; k < G; ++k) {
             const bool pend = und[k] != 0u;

@@ -66,6 +66,8 @@ _SIGS = {
     "ising_batch_observables": (ctypes.c_int, [_vp, _i32, _P(_i64), _P(_i64)]),
     "ising_batch_gather": (ctypes.c_int, [_vp, _i32, _P(_i32), _vp]),
     "ising_batch_specialized": (ctypes.c_int, [_vp, _P(_i32)]),
+    "ising_batch_set_cluster": (ctypes.c_int, [_vp, _i32]),
+    "ising_batch_cluster_size": (ctypes.c_int, [_vp, _P(_i32)]),
     "ising_batch_observables_ex": (ctypes.c_int, [_vp, _i32, _P(_i64), _P(_i64), _P(_i64)]),
     "ising_batch_history": (ctypes.c_int, [_vp, _i32, _i64, _i64, _P(_i64), _P(_i64)]),
     "ising_batch_moments": (ctypes.c_int, [_vp, _i32, _i64, _P(_d), _P(_u64)]),
@@ -218,6 +220,7 @@ def ising_batch_observables(b: int, idx: int) -> tuple[int, int]:
 
 
 SPECIALIZE_OFF, SPECIALIZE_AUTO, SPECIALIZE_ALWAYS = 0, 1, 2
+CLUSTER_OFF, CLUSTER_AUTO, CLUSTER_ALWAYS = 0, 1, 2
 
 
 def ising_set_specialize(mode: int) -> None:
@@ -490,6 +493,17 @@ class Batch:
         flag = ctypes.c_int32()
         _check(lib().ising_batch_specialized(self.b, ctypes.byref(flag)))
         return bool(flag.value)
+
+    def set_cluster(self, mode: int) -> None:
+        """CLUSTER_OFF, CLUSTER_AUTO (default) or CLUSTER_ALWAYS: when a batch of one
+        side L <= 4096 keeps its lattices in thread-block clusters."""
+        _check(lib().ising_batch_set_cluster(self.b, int(mode)))
+
+    def cluster_size(self) -> int:
+        """CTAs per cluster of the cluster-resident sweep, 0 on the tiled kernel."""
+        c = ctypes.c_int32()
+        _check(lib().ising_batch_cluster_size(self.b, ctypes.byref(c)))
+        return c.value
 
     def gather(self, idx, out_ptr: int) -> None:
         """Enqueue (sweeps done, M, E) of slots idx into out_ptr (3 int64 each,

@@ -363,3 +363,18 @@ def test_batch_gather_arguments(lib):
     out = (ctypes.c_int64 * 3)()
     assert lib.ising_batch_gather(None, 1, idx, out) == ising.ISING_EINVAL
     assert list(out) == [0, 0, 0]
+
+
+def test_batch_cluster_arguments(lib):
+    """ising_batch_set_cluster and ising_batch_cluster_size refuse a null batch (and
+    the mode constants agree with the header's)."""
+    assert (ising.CLUSTER_OFF, ising.CLUSTER_AUTO, ising.CLUSTER_ALWAYS) == (0, 1, 2)
+    for mode in (0, 1, 2, 3):
+        assert lib.ising_batch_set_cluster(None, mode) == ising.ISING_EINVAL
+    c = ctypes.c_int32(5)
+    assert lib.ising_batch_cluster_size(None, ctypes.byref(c)) == ising.ISING_EINVAL
+    assert c.value == 5
+    with open(os.path.join(ROOT, "include", "ising.h")) as f:
+        header = f.read()
+    for name, v in (("OFF", 0), ("AUTO", 1), ("ALWAYS", 2)):
+        assert f"#define ISING_CLUSTER_{name} {v}" in header
