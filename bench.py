@@ -189,6 +189,73 @@ def committed_counters(kernel: str):
             "capture": d.get("command")}
 
 
+# Counted model of the method's own integer work (the algorithmic view of the roofline).
+# Per 32-site plane word and half-sweep: E Philox calls (see expected_calls_per_word),
+# each 16 site-dependent 32x32->64 products and 18 three-input XORs; 4 logic operations
+# per bit plane the comparison reads (4 planes per call); a 15-operation bitwise adder.
+PHILOX_PRODUCTS_PER_CALL = 16
+PHILOX_XOR3_PER_CALL = 18
+COMPARE_OPS_PER_PLANE = 4
+ADDER_OPS_PER_WORD = 15
+
+
+def expected_calls_per_word(n):
+    """Expected Philox calls of a 32-site word with n tested sites.  U < T is read from
+    U's top bit plane down, four planes per call, and a tested site is decided at the
+    first plane where U's bit differs from T's: probability 1/2 per plane, independently
+    (T strictly between 0 and 2^32).  So call k (0-based) is needed iff some site is
+    still undecided after 4k planes: E = sum_k 1 - (1 - 2^-4k)^n, k = 0..7 (n = 0: no
+    call)."""
+    import numpy as np
+
+    n = np.asarray(n, dtype=np.float64)
+    return sum(1.0 - (1.0 - 2.0 ** (-4 * k)) ** n for k in range(8))
+
+
+def tested_sites_per_word(rows, test2: bool, test4: bool, first_row: int = 1):
+    """Tested sites per plane word for the centre rows of `rows` (R + 2 consecutive rows
+    of +-1 bytes, the first and last only as neighbours; the second has global index
+    first_row), both colours: a site with one anti-aligned neighbour compares against
+    T2 (test2: 0 < T2 < 2^32), with none against T4; bit b of word w of row i of colour
+    c is the site (i, 2(32w + b) + ((i + c) & 1))."""
+    import numpy as np
+
+    s = np.asarray(rows, dtype=np.int8)
+    c = s[1:-1]
+    n = ((s[:-2] != c).astype(np.int8) + (s[2:] != c) + (np.roll(c, 1, axis=1) != c)
+         + (np.roll(c, -1, axis=1) != c))
+    tested = ((n == 1) & test2) | ((n == 0) & test4)
+    R, L = c.shape
+    out = []
+    for i in range(R):
+        for colour in (0, 1):
+            out.append(tested[i, ((first_row + i + colour) & 1)::2].reshape(L // 64, 32).sum(axis=1))
+    return np.concatenate(out)
+
+
+def algorithmic_view(rows, T2: int, T4: int, sites_per_s: float, sm_max: float) -> dict:
+    """The roofline of the counted model: per site, E products x 2 lane-cycles on the
+    FMA-heavy pipe (a 32x32->64 product holds a 16-lane pipe 4 cycles per warp) / 32,
+    and (18 E + 16 E + 15) one-lane-cycle logic operations on the ALU pipe / 32, against
+    64 lanes/clk/SM x 152 SMs x the clock on each pipe."""
+    import numpy as np
+
+    n = tested_sites_per_word(rows, 0 < T2 < 2 ** 32, 0 < T4 < 2 ** 32)
+    E = float(np.mean(expected_calls_per_word(n)))
+    peak = ALU_OPS_PER_CLK_SM * N_SMS * sm_max * 1e6 / 1e12
+    fma = E * PHILOX_PRODUCTS_PER_CALL * 2.0 / 32.0
+    alu = (E * (PHILOX_XOR3_PER_CALL + 4 * COMPARE_OPS_PER_PLANE) + ADDER_OPS_PER_WORD) / 32.0
+    views = {name: {"lane_cycles_per_site": v, "achieved": v * sites_per_s / 1e12,
+                    "frac": v * sites_per_s / 1e12 / peak} for name, v in (("fmaheavy", fma), ("alu", alu))}
+    bind = max(views, key=lambda k: views[k]["frac"])
+    return {"frac": views[bind]["frac"], "pipe": PIPE_NAMES[bind], "calls_per_word": E,
+            "tested_sites_per_word": float(np.mean(n)), "words_sampled": int(n.size),
+            "views": {PIPE_NAMES[k]: v for k, v in views.items()}, "peak": peak, "unit": "Tops/s",
+            "model": "per 32-site word: E Philox calls (16 products, 18 XOR3 each) + 4 logic ops per bit plane "
+                     "read (4 per call) + 15 adder ops; E from the tested sites of each word of a sample of the "
+                     "final state (expected_calls_per_word); no queue, index or load/store work counted"}
+
+
 PIPE_NAMES = {"alu": "ALU pipe (logic, shifts, compares)",
               "fmaheavy": "FMA-heavy pipe (integer multiplies: the Philox products)"}
 
@@ -737,6 +804,12 @@ def main() -> None:
         roofline = kernel_roofline("int8_half_sweep", N / 2, t_launch_s, sm_max, peaks, bytes_per_site=INT8_BYTES_PER_SITE)
     roofline["probe_alu_ops_per_clk_sm"] = alu_per_clk
     roofline["probe_mul_xor_steps_per_clk_sm"] = mul_per_clk
+    if kernel == ising.PACKED:
+        # the counted model's fraction beside the executed one, from 64 rows of the state
+        T2, T4 = ising.ising_thresholds(cfg.beta)
+        nrow = min(66, L)
+        roofline["algorithmic"] = algorithmic_view(lat.get_rows(0, nrow), T2, T4, (N / 2) / t_launch_s, sm_max)
+        roofline["algorithmic"]["sample"] = f"rows 1..{nrow - 2} of the state after the timed sweeps"
 
     # the same K timed steps again, for the run-to-run spread (the lattice continues its chain)
     reps = []

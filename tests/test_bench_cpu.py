@@ -119,3 +119,70 @@ def test_profile_commands_still_run_as_written():
             assert "python bench.py" in line, (name, line)
         argv = line.split("python bench.py", 1)[1].split()
         bench.make_parser().parse_args(argv)
+
+
+def test_expected_calls_per_word_matches_a_simulation():
+    """E[calls] of the counted model against a direct simulation of the bit-plane
+    comparison: n sites with random 32-bit U and a fixed T, read four planes per call
+    from the top; a word draws call k iff some site is undecided after 4k planes."""
+    import numpy as np
+
+    rng = np.random.default_rng(7)
+    T = 0x2BEC3A1F
+    for n in (0, 1, 3, 16, 32):
+        words = 20000
+        calls = np.zeros(words)
+        if n:
+            U = rng.integers(0, 2 ** 32, size=(words, n), dtype=np.uint64)
+            # planes read by each site: the position (from the top) of the first bit
+            # where U and T differ, plus one
+            diff = U ^ np.uint64(T)
+            planes = 32 - np.floor(np.log2(diff.astype(np.float64))).astype(int)
+            calls = np.ceil(planes.max(axis=1) / 4.0)
+        assert np.mean(calls) == pytest.approx(float(bench.expected_calls_per_word(n)), abs=0.02), n
+    assert float(bench.expected_calls_per_word(0)) == 0.0
+    assert float(bench.expected_calls_per_word(1)) == pytest.approx(sum(2.0 ** (-4 * k) for k in range(8)))
+
+
+def test_tested_sites_per_word_by_brute_force():
+    """Per-word tested-site counts against a site-by-site loop over the plane layout."""
+    import numpy as np
+
+    rng = np.random.default_rng(3)
+    L, R, first = 128, 5, 7
+    rows = rng.choice(np.array([-1, 1], dtype=np.int8), size=(R + 2, L))
+    got = bench.tested_sites_per_word(rows, True, False, first_row=first)
+    want = []
+    for i in range(R):
+        gi = first + i
+        for colour in (0, 1):
+            for w in range(L // 64):
+                cnt = 0
+                for b in range(32):
+                    j = 2 * (32 * w + b) + ((gi + colour) & 1)
+                    s = rows[i + 1, j]
+                    n = sum(int(x != s) for x in (rows[i, j], rows[i + 2, j], rows[i + 1, (j - 1) % L],
+                                                   rows[i + 1, (j + 1) % L]))
+                    cnt += n == 1
+                want.append(cnt)
+    assert list(got) == want
+    both = bench.tested_sites_per_word(rows, True, True, first_row=first)
+    assert np.all(both >= got) and both.sum() > got.sum()
+
+
+def test_algorithmic_view_arithmetic():
+    """All sites tested with one threshold: E = expected_calls_per_word(32); the views are
+    E products x 2 lane-cycles / 32 (FMA-heavy) and (34 E + 15) / 32 (ALU) per site."""
+    import numpy as np
+
+    rows = np.ones((4, 128), dtype=np.int8)  # all aligned: every site has n = 0
+    v = bench.algorithmic_view(rows, 2 ** 32, 5 << 28, 1e12, 2070.0)
+    E = float(bench.expected_calls_per_word(32))
+    assert v["calls_per_word"] == pytest.approx(E) and v["tested_sites_per_word"] == 32
+    peak = 64 * 152 * 2070.0 * 1e6 / 1e12
+    alu = (34 * E + 15) / 32
+    assert v["views"][bench.PIPE_NAMES["alu"]]["frac"] == pytest.approx(alu * 1e12 / 1e12 / peak)
+    assert v["views"][bench.PIPE_NAMES["fmaheavy"]]["lane_cycles_per_site"] == pytest.approx(E)
+    assert v["frac"] == pytest.approx(max(alu, E) / peak)
+    # a threshold of 2^32 (accept all) or 0 tests nothing
+    assert bench.algorithmic_view(rows, 2 ** 32, 2 ** 32, 1e12, 2070.0)["calls_per_word"] == 0.0
