@@ -181,11 +181,16 @@ def committed_counters(kernel: str):
     alu = d.get("alu_warp_inst_per_launch")
     pipes = {name: d[f"{name}_pipe_cycles_per_launch"] / sites for name in ("alu", "fmaheavy")
              if f"{name}_pipe_cycles_per_launch" in d}
+    # DRAM bytes per site from a one-pass capture of the full-size workload where the
+    # record has one (re-reads depend on the lattice's size), else from the small case
+    fs = d.get("full_size")
+    dram = ((fs["dram_bytes_read_per_launch"] + fs["dram_bytes_write_per_launch"]) / fs["sites_per_launch"] if fs
+            else (d["dram_bytes_read_per_launch"] + d["dram_bytes_write_per_launch"]) / sites)
     return {"current": d.get("kernel_source_hash") == kernel_source_hash(kernel),
             "inst_slots_per_site": 32.0 * d["warp_inst_per_launch"] / sites,
             "alu_ops_per_site": None if alu is None else 32.0 * alu / sites,
             "pipe_cycles_per_site": pipes or None,
-            "dram_bytes_per_site": (d["dram_bytes_read_per_launch"] + d["dram_bytes_write_per_launch"]) / sites,
+            "dram_bytes_per_site": dram,
             "capture": d.get("command")}
 
 

@@ -462,6 +462,7 @@ struct ising_s {
     int64_t hist_cap = 0;
     int64_t sweeps_done = 0;
     int64_t* d_me0 = nullptr;   // start-state (M, E)
+    unsigned long long* d_work3 = nullptr;  // 3D: the half-sweeps' work counters (one per colour)
     double* d_mom = nullptr;    // 6 doubles
     uint64_t* d_sums = nullptr; // 11 limbs
     std::string kernel_note;    // which sweep kernel runs, and why (ising_specialized)
@@ -665,6 +666,7 @@ void destroy_handle(ising_t h)
     cudaFree(h->lat);
     cudaFree(h->hist);
     cudaFree(h->d_me0);
+    cudaFree(h->d_work3);
     cudaFree(h->d_mom);
     cudaFree(h->d_sums);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
@@ -883,6 +885,8 @@ int ising_init3d(ising_t* out, int64_t L, double beta, uint64_t seed, int start,
     if (e == cudaSuccess) e = cudaMalloc(&h->d_mom, 6 * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&h->d_sums, 11 * sizeof(uint64_t));
     if (e == cudaSuccess) e = cudaMalloc(&h->planes, sizeof(uint32_t) * 2 * (size_t)plane_words(h));
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_work3, 2 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->d_work3, 0, 2 * sizeof(unsigned long long), h->stream);
     if (e == cudaSuccess) e = launch_cubic_init(h->planes, h->planes + plane_words(h), L, seed, start, h->stream);
     rc = (e == cudaSuccess) ? ensure_hist(h, 1024) : cuda_fail(e, "3D lattice set-up");
     if (!rc) rc = refresh_me0(h);
@@ -924,7 +928,7 @@ int ising_sweep(ising_t h, int64_t n)
         const CubicDesc d = cubic_desc(h);
         for (int64_t k = 0; k < n; ++k)
             for (int c = 0; c < 2; ++c) {
-                cudaError_t e = launch_cubic_half_sweep(d, c, (uint32_t)(h->sweeps_done + k), h->stream,
+                cudaError_t e = launch_cubic_half_sweep(d, h->d_work3, c, (uint32_t)(h->sweeps_done + k), h->stream,
                                                         h->cubic_fixed[0] ? h->cubic_fixed : nullptr);
                 if (e != cudaSuccess) return cuda_fail(e, "3D half-sweep launch");
             }

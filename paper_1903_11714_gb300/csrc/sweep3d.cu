@@ -113,8 +113,8 @@ cudaError_t launch_cubic_observe(const uint32_t* black, const uint32_t* white, i
 
 int cubic_words_per_group(int64_t L) { return (L / 64) % 4 == 0 ? 4 : 1; }
 
-cudaError_t launch_cubic_half_sweep(const CubicDesc& d, int colour, uint32_t sweep, cudaStream_t s,
-                                    const void* const* fixed)
+cudaError_t launch_cubic_half_sweep(const CubicDesc& d, unsigned long long* work, int colour, uint32_t sweep,
+                                    cudaStream_t s, const void* const* fixed)
 {
     const int64_t L = d.L, W = d.W;
     const int G = cubic_words_per_group(L);
@@ -125,17 +125,17 @@ cudaError_t launch_cubic_half_sweep(const CubicDesc& d, int colour, uint32_t swe
     if (fixed && fixed[colour]) {
         // the instance compiled for this lattice's thresholds (jit.cu), same parameters
         CubicDesc dd = d;
-        void* args[] = {&dd, &colour, &sweep};
+        void* args[] = {&dd, &colour, &sweep, &work};
         return cudaLaunchKernel(fixed[colour], dim3(grid), dim3(kThreads3), args, 0, s);
     }
     if (G == 4 && colour == 1)
-        cubic_half_sweep_kernel<kThreads3, 4, true><<<grid, kThreads3, 0, s>>>(d, colour, sweep);
+        cubic_half_sweep_kernel<kThreads3, 4, true><<<grid, kThreads3, 0, s>>>(d, colour, sweep, work);
     else if (G == 4)
-        cubic_half_sweep_kernel<kThreads3, 4, false><<<grid, kThreads3, 0, s>>>(d, colour, sweep);
+        cubic_half_sweep_kernel<kThreads3, 4, false><<<grid, kThreads3, 0, s>>>(d, colour, sweep, work);
     else if (colour == 1)
-        cubic_half_sweep_kernel<kThreads3, 1, true><<<grid, kThreads3, 0, s>>>(d, colour, sweep);
+        cubic_half_sweep_kernel<kThreads3, 1, true><<<grid, kThreads3, 0, s>>>(d, colour, sweep, work);
     else
-        cubic_half_sweep_kernel<kThreads3, 1, false><<<grid, kThreads3, 0, s>>>(d, colour, sweep);
+        cubic_half_sweep_kernel<kThreads3, 1, false><<<grid, kThreads3, 0, s>>>(d, colour, sweep, work);
     return cudaGetLastError();
 }
 

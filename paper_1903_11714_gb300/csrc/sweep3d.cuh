@@ -21,11 +21,13 @@ cudaError_t launch_cubic_init(uint32_t* black, uint32_t* white, int64_t L, uint6
 cudaError_t launch_cubic_observe(const uint32_t* black, const uint32_t* white, int64_t L, int64_t* ME,
                                  cudaStream_t s);
 // One half-sweep of colour `colour` of sweep `sweep`; the colour-0 launch opens
-// hist[sweep] and the colour-1 launch adds the fused (M, E) counts.  fixed (may be
-// null): the two colours' instances compiled for the lattice's thresholds
-// (jit_cubic_kernels), launched instead of the built-in ones.
-cudaError_t launch_cubic_half_sweep(const CubicDesc& d, int colour, uint32_t sweep, cudaStream_t s,
-                                    const void* const* fixed = nullptr);
+// hist[sweep] and the colour-1 launch adds the fused (M, E) counts.  work: the
+// lattice's two work counters (device memory, zero before its first half-sweep; the
+// launches keep them so).  fixed (may be null): the two colours' instances compiled
+// for the lattice's thresholds (jit_cubic_kernels), launched instead of the built-in
+// ones.
+cudaError_t launch_cubic_half_sweep(const CubicDesc& d, unsigned long long* work, int colour, uint32_t sweep,
+                                    cudaStream_t s, const void* const* fixed = nullptr);
 // Words per thread group of the 3D sweep for side L (4 when L/64 is a multiple of 4).
 int cubic_words_per_group(int64_t L);
 constexpr int kCubicThreads = 256;

@@ -220,9 +220,18 @@ __device__ __forceinline__ void block_add_twice(unsigned long long a, unsigned l
 // as far as decided, then final (ordered by __syncwarp).  COUNT (the colour-1 pass)
 // adds the fused observables; as a template parameter it leaves the colour-0 pass
 // without their instructions.
+//
+// Work order: each warp takes the next 8 x 32 word groups (rows in plane order) from
+// the counter work[colour] and its lanes walk them 32 consecutive groups at a time.
+// So the groups in flight always form one narrow band that moves through the plane,
+// and the source rows of slices i - 1 and i + 1 are read while they are still in L2
+// (with a fixed grid-stride split the CTAs drift apart over a half-sweep and a row
+// loaded for slice i - 1 is evicted before slice i + 1 needs it).  work[colour] is zero
+// at launch: the launch of the other colour, which runs before it on the stream,
+// clears it (and this launch clears work[colour ^ 1] for the next one).
 template <int NT, int G, bool COUNT, typename TH = RuntimeThresholds3>
 __global__ void __launch_bounds__(NT, 2) cubic_half_sweep_kernel(const __grid_constant__ CubicDesc d, int colour,
-                                                                 uint32_t sweep)
+                                                                 uint32_t sweep, unsigned long long* work)
 {
     __shared__ unsigned long long red[2 * (NT / 32)];
     __shared__ uint4 queues[(NT / 32) * 2 * kQueueCap3];
@@ -254,114 +263,124 @@ __global__ void __launch_bounds__(NT, 2) cubic_half_sweep_kernel(const __grid_co
     // L^3 / (2 * 152 * 2 * 8) white sites (< 1.2e8 at L = 8192) with at most 7
     // counted bits each
     uint32_t ups = 0, anti = 0;
-    // (i, j, word group) of g = start + k * stride, advanced without divisions: the
-    // stride is step_w groups within a row plus step_r rows, step_r = step_i * L + step_j
-    const int64_t start = (int64_t)blockIdx.x * NT + threadIdx.x;
-    const int64_t stride = (int64_t)gridDim.x * NT;
+    // (i, j, word group) of a lane's group, advanced by 32 groups per step without
+    // divisions: step_w groups within a row plus step_r rows, step_r = step_i * L + step_j
+    constexpr int kSteps = 8;
+    const int64_t stride = 32;
     const int64_t step_r = stride / WG;
     const int step_w = (int)(stride - step_r * WG);
     const int64_t step_i = step_r / L, step_j = step_r - step_i * L;
     int64_t i = 0, j = 0;
     int wg = 0;
-    if (start < ngroups) {
-        const int64_t r0 = start / WG;
-        wg = (int)(start - r0 * WG);
-        i = r0 / L;
-        j = r0 - i * L;
-    }
     // word offset of row (i, j), carried along the walk, and the offsets from it to
     // the rows (i-+1, j) and (i, j-+1) away from / across the torus seam
     const int64_t Wl = W, LW = L * Wl, LLW = L * LW;
     const int64_t step_off = step_r * Wl;
-    int64_t row = (i * L + j) * Wl;
-    // every lane runs every step (the votes and the queue need the whole warp); a
-    // lane past the end works on group 0 and keeps nothing
-    for (int64_t g0 = start - lane; g0 < ngroups; g0 += stride) {
-        const bool valid = g0 + lane < ngroups;
-        const int64_t vi = valid ? i : 0, vj = valid ? j : 0, vrow = valid ? row : 0;
-        const int w = valid ? wg * G : 0;
-        const int par = (int)((vi + vj + colour) & 1);
-        const int64_t up = vrow + (vi == 0 ? LLW - LW : -LW), dn = vrow + (vi == L - 1 ? LW - LLW : LW);
-        const int64_t no = vrow + (vj == 0 ? LW - Wl : -Wl), so = vrow + (vj == L - 1 ? Wl - LW : Wl);
-        Nbr<G> n;
-        load_neighbours_at<G>(src, W, vrow, up, dn, no, so, w, par, n);
-        uint32_t* trow = tgt + vrow + w;
-        uint32_t t[G];
-        if constexpr (G == 4) {
-            const uint4 q = *reinterpret_cast<const uint4*>(trow);
-            t[0] = q.x;
-            t[1] = q.y;
-            t[2] = q.z;
-            t[3] = q.w;
-        } else {
-#pragma unroll
-            for (int k = 0; k < G; ++k) t[k] = trow[k];
+    int64_t row = 0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) work[colour ^ 1] = 0ull;
+    for (;;) {
+        unsigned long long taken = 0ull;
+        if (lane == 0) taken = atomicAdd(work + colour, 32ull * kSteps);
+        const int64_t base = (int64_t)__shfl_sync(0xffffffffu, taken, 0);
+        if (base >= ngroups) break;
+        {
+            const int64_t r0 = (base + lane) / WG;
+            wg = (int)(base + lane - r0 * WG);
+            i = r0 / L;
+            j = r0 - i * L;
+            row = r0 * Wl;
         }
-        // q0 = r * (L/8) + 8w = 8 * (row + w) with L/8 = 8W; it is a multiple of 8 * G,
-        // so the group's calls q0 .. q0 + 8G - 1 share q's high word
-        const uint64_t q0 = 8ull * (uint64_t)(vrow + w);
-        const PhiloxWordConsts pc =
-            q_small ? pc_all : philox_consts(d.key, (uint32_t)(q0 >> 32), sweep, (uint32_t)colour);
-        uint32_t f[G], und[G], selA[G], selB[G], ql[G];
-#pragma unroll
-        for (int k = 0; k < G; ++k) {
-            uint32_t anti0;
-            classify_word3d(t[k], n.up[k], n.dn[k], n.no[k], n.so[k], n.sm[k], n.hz[k], all2, all4, all6, zero2,
-                            zero4, zero6, f[k], und[k], selA[k], selB[k], anti0);
-            if (!valid) und[k] = 0u;
-            if (COUNT && valid) {
-                ups += __popc(n.sm[k]);
-                anti += anti0;
-            }
-            ql[k] = (uint32_t)q0 + 8u * k;
-        }
-        // calls 0-1: nearly every warp needs both, so both are drawn without a vote
-        bitsliced_below<G, 3, 0, 2, true, false>(und, f, selA, selB, ql, pc, d.key, thr);
-        uint32_t nw[G];
-#pragma unroll
-        for (int k = 0; k < G; ++k) nw[k] = t[k] ^ f[k];
-        if (valid) {
+        // every lane runs every step (the votes and the queue need the whole warp); a
+        // lane past the end works on group 0 and keeps nothing
+        for (int s = 0; s < kSteps; ++s) {
+            const int64_t g0 = base + 32 * s;
+            if (g0 >= ngroups) break;
+            const bool valid = g0 + lane < ngroups;
+            const int64_t vi = valid ? i : 0, vj = valid ? j : 0, vrow = valid ? row : 0;
+            const int w = valid ? wg * G : 0;
+            const int par = (int)((vi + vj + colour) & 1);
+            const int64_t up = vrow + (vi == 0 ? LLW - LW : -LW), dn = vrow + (vi == L - 1 ? LW - LLW : LW);
+            const int64_t no = vrow + (vj == 0 ? LW - Wl : -Wl), so = vrow + (vj == L - 1 ? Wl - LW : Wl);
+            Nbr<G> n;
+            load_neighbours_at<G>(src, W, vrow, up, dn, no, so, w, par, n);
+            uint32_t* trow = tgt + vrow + w;
+            uint32_t t[G];
             if constexpr (G == 4) {
-                *reinterpret_cast<uint4*>(trow) = make_uint4(nw[0], nw[1], nw[2], nw[3]);
+                const uint4 q = *reinterpret_cast<const uint4*>(trow);
+                t[0] = q.x;
+                t[1] = q.y;
+                t[2] = q.z;
+                t[3] = q.w;
             } else {
-#pragma unroll
-                for (int k = 0; k < G; ++k) trow[k] = nw[k];
+    #pragma unroll
+                for (int k = 0; k < G; ++k) t[k] = trow[k];
             }
-        }
-#pragma unroll
-        for (int k = 0; k < G; ++k) {
-            const bool pend = und[k] != 0u;
-            if (COUNT && valid && !pend) {
-                ups += __popc(nw[k]);
-                anti += 6u * __popc(f[k]) - 2u * __popc(f[k] & selB[k]) - 4u * __popc(f[k] & selA[k]);
+            // q0 = r * (L/8) + 8w = 8 * (row + w) with L/8 = 8W; it is a multiple of 8 * G,
+            // so the group's calls q0 .. q0 + 8G - 1 share q's high word
+            const uint64_t q0 = 8ull * (uint64_t)(vrow + w);
+            const PhiloxWordConsts pc =
+                q_small ? pc_all : philox_consts(d.key, (uint32_t)(q0 >> 32), sweep, (uint32_t)colour);
+            uint32_t f[G], und[G], selA[G], selB[G], ql[G];
+    #pragma unroll
+            for (int k = 0; k < G; ++k) {
+                uint32_t anti0;
+                classify_word3d(t[k], n.up[k], n.dn[k], n.no[k], n.so[k], n.sm[k], n.hz[k], all2, all4, all6, zero2,
+                                zero4, zero6, f[k], und[k], selA[k], selB[k], anti0);
+                if (!valid) und[k] = 0u;
+                if (COUNT && valid) {
+                    ups += __popc(n.sm[k]);
+                    anti += anti0;
+                }
+                ql[k] = (uint32_t)q0 + 8u * k;
             }
-            const uint32_t bal = __ballot_sync(0xffffffffu, pend);
-            if (pend) {
-                const int slot = qn + __popc(bal & ((1u << lane) - 1u));
-                const uint64_t pos = (uint64_t)(vrow + w + k);
-                wq[2 * slot] = make_uint4((uint32_t)pos, (uint32_t)(pos >> 32), und[k], f[k]);
-                wq[2 * slot + 1] = make_uint4(selA[k], selB[k], t[k], 0u);
+            // calls 0-1: nearly every warp needs both, so both are drawn without a vote
+            bitsliced_below<G, 3, 0, 2, true, false>(und, f, selA, selB, ql, pc, d.key, thr);
+            uint32_t nw[G];
+    #pragma unroll
+            for (int k = 0; k < G; ++k) nw[k] = t[k] ^ f[k];
+            if (valid) {
+                if constexpr (G == 4) {
+                    *reinterpret_cast<uint4*>(trow) = make_uint4(nw[0], nw[1], nw[2], nw[3]);
+                } else {
+    #pragma unroll
+                    for (int k = 0; k < G; ++k) trow[k] = nw[k];
+                }
             }
-            qn += __popc(bal);
-        }
-        if (qn >= 32) {
-            __syncwarp();  // pushes visible to the draining lanes
-            do {
-                drain_queue3d<COUNT, TH>(d, tgt, pc_all, q_small, colour, sweep, wq, qn, 32, lane, ups, anti);
-            } while (qn >= 32);
-        }
-        wg += step_w;
-        j += step_j;
-        i += step_i;
-        row += step_off;
-        if (wg >= WG) {
-            wg -= WG;
-            ++j;
-            row += Wl;
-        }
-        if (j >= L) {
-            j -= L;
-            ++i;
+    #pragma unroll
+            for (int k = 0; k < G; ++k) {
+                const bool pend = und[k] != 0u;
+                if (COUNT && valid && !pend) {
+                    ups += __popc(nw[k]);
+                    anti += 6u * __popc(f[k]) - 2u * __popc(f[k] & selB[k]) - 4u * __popc(f[k] & selA[k]);
+                }
+                const uint32_t bal = __ballot_sync(0xffffffffu, pend);
+                if (pend) {
+                    const int slot = qn + __popc(bal & ((1u << lane) - 1u));
+                    const uint64_t pos = (uint64_t)(vrow + w + k);
+                    wq[2 * slot] = make_uint4((uint32_t)pos, (uint32_t)(pos >> 32), und[k], f[k]);
+                    wq[2 * slot + 1] = make_uint4(selA[k], selB[k], t[k], 0u);
+                }
+                qn += __popc(bal);
+            }
+            if (qn >= 32) {
+                __syncwarp();  // pushes visible to the draining lanes
+                do {
+                    drain_queue3d<COUNT, TH>(d, tgt, pc_all, q_small, colour, sweep, wq, qn, 32, lane, ups, anti);
+                } while (qn >= 32);
+            }
+            wg += step_w;
+            j += step_j;
+            i += step_i;
+            row += step_off;
+            if (wg >= WG) {
+                wg -= WG;
+                ++j;
+                row += Wl;
+            }
+            if (j >= L) {
+                j -= L;
+                ++i;
+            }
         }
     }
     if (qn > 0) {

@@ -186,3 +186,17 @@ def test_algorithmic_view_arithmetic():
     assert v["frac"] == pytest.approx(max(alu, E) / peak)
     # a threshold of 2^32 (accept all) or 0 tests nothing
     assert bench.algorithmic_view(rows, 2 ** 32, 2 ** 32, 1e12, 2070.0)["calls_per_word"] == 0.0
+
+
+def test_full_size_traffic_is_preferred():
+    """A record with a one-pass full-size DRAM capture reports that capture's bytes per
+    site (the cube's re-reads, if any, depend on its size)."""
+    with open(os.path.join(ROOT, "profiles", "cubic_half_sweep_counters.json")) as f:
+        d = json.load(f)
+    fs = d["full_size"]
+    c = bench.committed_counters("cubic_half_sweep")
+    want = (fs["dram_bytes_read_per_launch"] + fs["dram_bytes_write_per_launch"]) / fs["sites_per_launch"]
+    assert c["dram_bytes_per_site"] == pytest.approx(want)
+    assert "--clock-control none" in fs["command"]
+    # at most the algorithmic bytes plus 5 %: each plane read once, the target written once
+    assert fs["dram_bytes_read_per_launch"] + fs["dram_bytes_write_per_launch"] <= 1.05 * fs["algorithmic_bytes_per_launch"]
