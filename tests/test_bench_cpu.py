@@ -200,3 +200,20 @@ def test_full_size_traffic_is_preferred():
     assert "--clock-control none" in fs["command"]
     # at most the algorithmic bytes plus 5 %: each plane read once, the target written once
     assert fs["dram_bytes_read_per_launch"] + fs["dram_bytes_write_per_launch"] <= 1.05 * fs["algorithmic_bytes_per_launch"]
+
+
+def test_saturated_capacity_counts_the_work_of_unfinished_requests():
+    """Requests all admitted at t = 0 advance in lockstep: at the time the half-way
+    request finishes, each unfinished one has done as many sweeps as the longest
+    finished one.  Three requests of 100, 200, 400 sweeps (L = 64, 128, 256) and one of
+    800 (L = 64): after two finish (at t = 2.0 s, the 200-sweep one), the others have
+    done 200 sweeps each."""
+    from types import SimpleNamespace as R
+    res = [R(L=256, sweeps=400, finished=4.0), R(L=64, sweeps=100, finished=1.0),
+           R(L=64, sweeps=800, finished=8.0), R(L=128, sweeps=200, finished=2.0)]
+    work = 64 * 64 * 100 + 128 * 128 * 200 + 256 * 256 * 200 + 64 * 64 * 200
+    assert bench.saturated_capacity(res) == pytest.approx(work / 2.0, rel=1e-15)
+    # a request shorter than the finished ones' longest (collected later) counts whole
+    res.append(R(L=64, sweeps=150, finished=2.5))
+    work5 = 64 * 64 * 100 + 64 * 64 * 150 + 128 * 128 * 200 + 256 * 256 * 200 + 64 * 64 * 200
+    assert bench.saturated_capacity(res) == pytest.approx(work5 / 2.0, rel=1e-15)

@@ -35,8 +35,9 @@ class FakeBatch:
     def usage(self):
         return sum(v["bytes"] for v in self.live.values()), self.budget
 
-    def add(self, L, beta, seed, start, sweeps):
+    def add(self, L, beta, seed, start, sweeps, tile_rows=0):
         assert start == ising.HOT
+        assert tile_rows == serve.tile_rows(L)
         need = serve.Server.request_bytes(L, sweeps)
         if len(self.live) >= self.slots:
             raise ising.IsingError(ising.ISING_EBUSY, "no free slot")
@@ -218,3 +219,23 @@ def test_batch_workloads_follow_their_recipes():
     assert len(binder) == 36 and len({s.seed for s in binder}) == 36
     assert all(abs(s.beta * t - workloads.BETA_C_EXACT) < 1e-15
                for s, t in zip(binder, workloads.BINDER_T_OVER_TC * len(workloads.BINDER_LS)))
+
+
+def test_served_tiles_are_the_tallest_that_fit():
+    """Whole-row tiles of at most 8,192 words and 256 rows, a power of two dividing L,
+    for every side the request recipe can draw (L = 64 k, 4 <= k <= 128); each is a
+    shape the library accepts (2-row tiles need W % 4 == 0, 4+ rows any W)."""
+    for k in range(4, 129):
+        L = 64 * k
+        W, tr = L // 64, serve.tile_rows(L)
+        assert tr & (tr - 1) == 0 and 2 <= tr <= 256 and L % tr == 0
+        assert tr * W <= serve.TILE_WORDS
+        assert tr == 256 or 2 * tr * W > serve.TILE_WORDS or L % (2 * tr) != 0
+        assert tr >= 4 or W % 4 == 0
+        # the stage (the tile's source rows with HB halo rows each side -- 4 when W % 4
+        # != 0, so that copies stay 16-byte aligned -- and its target rows) fits the
+        # library's 100 KB stage cap
+        hb = 1 if W % 4 == 0 else 4
+        assert ((tr + 2 * hb) * W + tr * W) * 4 <= 100 * 1024
+    assert serve.tile_rows(8192) == 64 and serve.tile_rows(1024) == 256 and serve.tile_rows(64 * 127) == 64
+    assert serve.tile_rows(2560) == 128  # W = 40: 256 rows would be 10,240 words
