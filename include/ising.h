@@ -298,8 +298,10 @@ int ising_init3d(ising_t *out, int64_t L, double beta, uint64_t seed, int start,
  * simulations run as one replicated program, here one launch).
  * The lattices have no sweep limit: every ising_batch_run sweeps all of them, and
  * their (M, E) histories live outside the planes' arena and grow (doubling) when a
- * run needs room.  Built-in tile shapes, 256-thread CTAs (512 when a side is at least
- * 16,384), a stream the batch owns.
+ * run needs room.  Tiles: the tallest whole-row tile of at most 8,192 words for each
+ * lattice when the batch then holds at least two tiles per CTA of its persistent grid,
+ * else the built-in shapes; 256-thread CTAs (512 when a side is at least 16,384), a
+ * stream the batch owns.
  * EINVAL, before any device work, for a null array, count outside 1 .. 2^20, or
  * any bad L, beta or start (the message names the lattice).  ENOMEM, ECUDA.
  */

@@ -1406,6 +1406,22 @@ int ising_batch_add(ising_batch_t b, int64_t L, double beta, uint64_t seed, int3
     return ising_batch_add_tiled(b, L, beta, seed, start, sweeps, tile_rows, 0, idx);
 }
 
+// Tile height for a lattice of a batch known in full at creation: the tallest whole-row
+// tile of at most 8,192 words (256 rows at most, a power of two the stage holds), or 0
+// (the built-in height) for sides that take column blocks.  Taller tiles give each warp
+// more words per tile, so the per-tile costs (the stage handoff, the last partial drain
+// of each warp's queue) weigh less; they pay once the batch holds enough of them for
+// every CTA of the persistent grid (ising_batch_create).
+int tall_tile_rows(int64_t L)
+{
+    const int64_t W = L / 64;
+    if (default_tile_words(L) != (int)W) return 0;
+    int best = 0;
+    for (int tr = 2; tr <= kMaxTileRows; tr *= 2)
+        if (tile_rows_ok(L, tr) && (int64_t)tr * W <= 8192) best = tr;
+    return best;
+}
+
 int ising_batch_create(ising_batch_t* out, int32_t count, const int64_t* L, const double* beta, const uint64_t* seed,
                        const int32_t* start)
 {
@@ -1427,10 +1443,18 @@ int ising_batch_create(ising_batch_t* out, int32_t count, const int64_t* L, cons
     int rc = ising_batch_create_ex(&b, count, max_L, arena, max_L >= 16384 ? 512 : 256, nullptr);
     if (rc) return rc;
     b->growable = true;
+    // tall tiles when they still give every CTA of the persistent grid two tiles or more
+    int64_t tall_tiles = 0;
+    for (int32_t k = 0; k < count; ++k) {
+        const int tr = tall_tile_rows(L[k]);
+        tall_tiles += tr ? L[k] / tr : lattice_tiles(L[k], default_tile_rows(L[k], b->eng.threads), 0);
+    }
+    const bool tall = tall_tiles >= 2 * (int64_t)b->eng.grid;
     constexpr int64_t kFirstHistory = 1024;  // sweeps of history at admission, doubled as needed
     for (int32_t k = 0; k < count && !rc; ++k) {
         int32_t idx = -1;
-        rc = ising_batch_add(b, L[k], beta[k], seed[k], start[k], kFirstHistory, 0, &idx);
+        rc = ising_batch_add(b, L[k], beta[k], seed[k], start[k], kFirstHistory, tall ? tall_tile_rows(L[k]) : 0,
+                             &idx);
     }
     if (rc) {
         const std::string msg = t_error;
