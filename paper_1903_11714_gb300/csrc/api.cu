@@ -1412,7 +1412,7 @@ int ising_batch_add(ising_batch_t b, int64_t L, double beta, uint64_t seed, int3
 // more words per tile, so the per-tile costs (the stage handoff, the last partial drain
 // of each warp's queue) weigh less; they pay once the batch holds enough of them for
 // every CTA of the persistent grid (ising_batch_create).
-int tall_tile_rows(int64_t L)
+static int tall_tile_rows(int64_t L)
 {
     const int64_t W = L / 64;
     if (default_tile_words(L) != (int)W) return 0;
