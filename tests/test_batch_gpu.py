@@ -253,6 +253,29 @@ def test_batch_from_arrays_matches_oracle_through_history_growth():
         b.close()
 
 
+def test_array_form_with_tall_tiles_matches_oracle():
+    """A batch created from arrays with enough lattices that ising_batch_create gives
+    each the tallest whole-row tile of up to 8,192 words (here one tile per L = 128
+    lattice and three 64-row tiles per L = 192 lattice, whose odd row width needs
+    4-row halos: 1,280 tiles, over two per CTA of the grid), swept as a captured
+    graph: every lattice and every sweep's M and E equal the oracle's."""
+    n_each, sweeps = 320, 4
+    Ls = [128] * n_each + [192] * n_each
+    betas = [0.30 + 0.3 * k / (2 * n_each) for k in range(2 * n_each)]
+    seeds = [5000 + k for k in range(2 * n_each)]
+    starts = [ising.HOT if k % 3 else ising.COLD for k in range(2 * n_each)]
+    b = ising.Batch.from_arrays(Ls, betas, seeds, starts)
+    try:
+        b.run(sweeps, graph_sweeps=2)
+        for k in range(2 * n_each):
+            ref, Mr, Er, _ = oracle.run(Ls[k], betas[k], seeds[k], starts[k], sweeps)
+            M, E = b.history(k)
+            assert np.array_equal(M, Mr) and np.array_equal(E, Er), k
+            assert np.array_equal(b.get_lattice(k), ref), k
+    finally:
+        b.close()
+
+
 def test_single_handle_moments_five_outputs_match_the_extended_form():
     """ising_moments (the boundary's five outputs) equals ising_moments_ex's values."""
     lat = ising.Lattice(256, 0.45, 5, ising.HOT, ising.PACKED).sweep(300)
