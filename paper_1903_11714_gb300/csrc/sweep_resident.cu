@@ -38,6 +38,22 @@ __global__ void __launch_bounds__(NT, 1) packed_resident_kernel(const __grid_con
     // thresholds 0 (never accept) are taken out of the test like 2^32 (always)
     const uint32_t zero2 = (d.t2 == 0u && d.all2 == 0u) ? ~0u : 0u, zero4 = (d.t4 == 0u && d.all4 == 0u) ? ~0u : 0u;
     const uint32_t thr[2] = {d.t2, d.t4};
+    // the thresholds' bits in planes 0 .. 4 * kFirstCalls - 1 as all-ones / all-zero
+    // masks, formed once per launch and held in registers (the opaque move keeps the
+    // compiler from forming them again, from the launch-uniform thresholds, in every
+    // plane of every half-sweep: six instructions a plane)
+    constexpr int kPlanes = 4 * kFirstCalls;
+    uint32_t K2[kPlanes], K4[kPlanes];
+#pragma unroll
+    for (int p = 0; p < kPlanes; ++p) {
+        K2[p] = 0u - ((d.t2 >> (31 - p)) & 1u);
+        K4[p] = 0u - ((d.t4 >> (31 - p)) & 1u);
+        asm volatile("mov.b32 %0, %0;" : "+r"(K2[p]));
+        asm volatile("mov.b32 %0, %0;" : "+r"(K4[p]));
+    }
+    // (row, word) of idx = tid + k * NT, advanced without a division
+    const int step_r = NT / W, step_w = NT - step_r * W;
+    const int i_first = tid / W, w_first = tid - i_first * W;
     for (int s = 0; s < nsweeps; ++s) {
         const uint32_t sweep = d.sweep + (uint32_t)s;
         for (int colour = 0; colour < 2; ++colour) {
@@ -45,8 +61,12 @@ __global__ void __launch_bounds__(NT, 1) packed_resident_kernel(const __grid_con
             uint32_t* tgt = pl[colour];
             const PhiloxWordConsts pc_all = philox_consts(key, 0u, sweep, (uint32_t)colour);
             uint32_t ups = 0, anti = 0;
-            for (int idx = tid; idx < words; idx += NT) {
-                const int i = idx / W, w = idx - i * W;
+            int i = i_first, w = w_first;
+            for (int idx = tid; idx < words; idx += NT, i += step_r, w += step_w) {
+                if (w >= W) {
+                    w -= W;
+                    ++i;
+                }
                 const int iu = i == 0 ? L - 1 : i - 1, id = i + 1 == L ? 0 : i + 1;
                 const uint32_t up = src[iu * W + w], down = src[id * W + w], same = src[idx];
                 uint32_t hz;
@@ -70,8 +90,7 @@ __global__ void __launch_bounds__(NT, 1) packed_resident_kernel(const __grid_con
                     for (int c = 0; c < kFirstCalls; ++c)
 #pragma unroll
                         for (int m = 0; m < 4; ++m) {
-                            const int bit = 31 - (4 * c + m);
-                            const uint32_t tm = (sel[0] & (0u - ((d.t2 >> bit) & 1u))) | (~sel[0] & (0u - ((d.t4 >> bit) & 1u)));
+                            const uint32_t tm = (sel[0] & K2[4 * c + m]) | (~sel[0] & K4[4 * c + m]);
                             const uint32_t x = und[0] & (o[c][m] ^ tm);  // decided in this plane
                             f[0] |= x & tm;                             // ... below: U's bit 0, T's bit 1
                             und[0] &= ~x;
@@ -95,15 +114,18 @@ __global__ void __launch_bounds__(NT, 1) packed_resident_kernel(const __grid_con
                 }
             }
             __syncthreads();
-            if (colour == 1 && tid == 0) {
-                int64_t su = 0, sa = 0;
-                for (int k = 0; k < NT / 32; ++k) {
-                    su += red[2 * k];
-                    sa += red[2 * k + 1];
+            if (colour == 1 && tid < 32) {
+                // the warps' partial sums added by the first warp; a lattice of at most
+                // 2^16 sites keeps every count far below 2^32
+                const uint32_t u = tid < NT / 32 ? red[2 * tid] : 0u;
+                const uint32_t a = tid < NT / 32 ? red[2 * tid + 1] : 0u;
+                const uint32_t su = __reduce_add_sync(0xffffffffu, u);
+                const uint32_t sa = __reduce_add_sync(0xffffffffu, a);
+                if (tid == 0) {
+                    const int64_t N = (int64_t)L * L;
+                    d.hist[2 * (int64_t)sweep] = 2 * (int64_t)su - N;
+                    d.hist[2 * (int64_t)sweep + 1] = 2 * (int64_t)sa - 2 * N;
                 }
-                const int64_t N = (int64_t)L * L;
-                d.hist[2 * (int64_t)sweep] = 2 * su - N;
-                d.hist[2 * (int64_t)sweep + 1] = 2 * sa - 2 * N;
             }
         }
     }
