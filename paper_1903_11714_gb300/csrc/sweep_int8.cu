@@ -136,8 +136,11 @@ __global__ void int8_half_sweep_seg64_kernel(int8_t* lat, int64_t L, uint64_t ke
         uint32_t lt[1] = {(h2m & all2) | (h4m & all4)};
         uint32_t und[1] = {(h2m & ~(all2 | zero2)) | (h4m & ~(all4 | zero4))};
         {
+            // calls 0-1 (planes 0-7) as straight-line code: a 32-site word with most of its
+            // sites tested needs both nearly always; the rest stop once the word is decided
             const uint32_t sel[1] = {h2m}, ql[1] = {(uint32_t)q0};
-            bitsliced_below<1, 2>(und, lt, sel, sel, ql, pcw, key, thr);
+            bitsliced_below<1, 2, 0, 2, false, false>(und, lt, sel, sel, ql, pcw, key, thr);
+            bitsliced_below<1, 2, 2, 8>(und, lt, sel, sel, ql, pcw, key, thr);
         }
         const uint32_t accm = alw | lt[0];
         uint32_t nw[16];
