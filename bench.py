@@ -926,6 +926,9 @@ def run_plain_int8(cfg, steps: int, warmup: int) -> dict:
             "note": "row-major int8 lattice (4.3 GB), each half-sweep reads and writes every byte"}
 
 
+E2E_RUNS = 3  # wall-clocked runs of the end-to-end measurement (host copies vary run to run)
+
+
 def measure_e2e(lat, L, cfg, steps, stream) -> dict:
     """Same metric through the C ABI with host buffers: upload the start planes
     from pinned host memory, sweep, read back the M/E history and the final planes."""
@@ -943,21 +946,27 @@ def measure_e2e(lat, L, cfg, steps, stream) -> dict:
     white[:] = w0
     del b0, w0
     e.close()
-    h = ising.Lattice(L, cfg.beta, cfg.seed, ising.COLD, ising.PACKED, stream=stream)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    h.set_planes(black, white)
-    h.sweep(steps)
-    M, E = h.history(0, steps)
-    h.get_planes(black, white)
-    dt = time.perf_counter() - t0
-    h.close()
+    start_b, start_w = black.copy(), white.copy()
+    values = []
+    for _ in range(E2E_RUNS):
+        black[:] = start_b
+        white[:] = start_w
+        h = ising.Lattice(L, cfg.beta, cfg.seed, ising.COLD, ising.PACKED, stream=stream)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h.set_planes(black, white)
+        h.sweep(steps)
+        M, E = h.history(0, steps)
+        h.get_planes(black, white)
+        dt = time.perf_counter() - t0
+        h.close()
+        values.append(steps * L * L / (dt * 1e9))
     h2d = 2 * words * 4
     d2h = 2 * words * 4 + 16 * steps
-    return {"value": steps * L * L / (dt * 1e9), "unit": UNIT, "h2d_bytes_per_step": h2d / steps,
-            "d2h_bytes_per_step": d2h / steps,
-            "note": "one run per measurement: start planes host->device, the sweeps, M/E history and final planes "
-                    "device->host, all pinned host buffers, wall clock"}
+    return {"value": statistics.median(values), "unit": UNIT, "h2d_bytes_per_step": h2d / steps,
+            "d2h_bytes_per_step": d2h / steps, "runs": values,
+            "note": f"median of {E2E_RUNS} runs, each on a fresh handle: start planes host->device, the sweeps, M/E "
+                    "history and final planes device->host, all pinned host buffers, wall clock"}
 
 
 if __name__ == "__main__":
